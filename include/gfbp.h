@@ -1,0 +1,169 @@
+/*
+ * gfbp — belief-propagation decoding of LDPC codes over GF(q), q = 2^p <= 256,
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: N. Yacov, H. Efraim, H. Kfir, I. Kanter, O. Shental, "Parallel vs.
+ * Sequential Belief Propagation Decoding of LDPC Codes over GF(q) and Markov
+ * Sources" (arXiv cs/0605069).  Section and equation numbers are the paper's.
+ *
+ * Conventions shared by every entry point
+ *   - Symbols are GF(2^p) elements 0..q-1; bit k of symbol a is (a >> k) & 1;
+ *     GF addition is XOR (Sec. 2: "r = t + n mod 2" on the binary image).
+ *   - Edges of H are ordered by (row, col); every per-edge array uses that order.
+ *   - "device" pointers are CUDA global-memory addresses of the current device;
+ *     "host" pointers are ordinary CPU memory.  The caller owns every buffer it
+ *     passes; the library keeps no pointer to caller memory after the call's
+ *     work on `stream` has completed.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     stream-ordered and asynchronous unless stated otherwise.
+ *   - Errors: every call returns a status.  Arguments are validated on the host
+ *     before any launch; on error nothing is launched and gfbp_last_error()
+ *     describes the cause.  No kernel traps; device-side anomalies are reported
+ *     through status words.
+ */
+#ifndef GFBP_H
+#define GFBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GFBP_OK = 0,
+    GFBP_EINVAL = 1,      /* invalid argument (reason in gfbp_last_error) */
+    GFBP_ENOMEM = 2,      /* host or device allocation failed */
+    GFBP_ECUDA = 3,       /* a CUDA runtime call failed */
+    GFBP_ETIMEOUT = 4,    /* a bounded wait ran out */
+    GFBP_EBUSY = 5,       /* resource in use (e.g. a full admission budget) */
+    GFBP_EUNSUPPORTED = 6 /* valid input outside what this build implements */
+} gfbp_status;
+
+/* Thread-local description of the last error of this thread's calls. */
+const char* gfbp_last_error(void);
+
+/* ------------------------------------------------------------------ code */
+typedef struct gfbp_code gfbp_code; /* opaque; owns a device copy of H */
+
+/*
+ * Build a code from the sparse parity-check matrix H (M x N) over GF(q)
+ * (Sec. 2: the non-zero elements of row i are the symbols of check i, those of
+ * column j the checks of symbol j; non-zero values are in {1..q-1}).
+ *   q          field size, 2^p with 1 <= p <= 8.
+ *   M, N       rows (checks) and columns (symbols); N >= 1, M >= 0.
+ *   nnz        number of non-zeros E.
+ *   row, col, val  host [nnz] COO triplets, 0 <= row < M, 0 <= col < N,
+ *              1 <= val < q, no duplicate (row, col); any order (the library
+ *              sorts by (row, col)).
+ *   prim_poly  field polynomial with bit k = coefficient of x^k (degree p, must
+ *              be primitive); 0 = default x^2+x+1, x^3+x+1, x^4+x+1, x^5+x^2+1,
+ *              x^6+x+1, x^7+x^3+1, x^8+x^4+x^3+x^2+1.
+ *   out        receives the handle.
+ * Synchronous: copies H to the current device before returning.  Row degree
+ * must be <= 16 and column degree <= 8 (GFBP_EUNSUPPORTED otherwise).
+ */
+gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t nnz, const int32_t* row,
+                             const int32_t* col, const int32_t* val, uint32_t prim_poly, gfbp_code** out);
+
+/* Release a code (synchronous; no decode using it may still be in flight). */
+void gfbp_code_destroy(gfbp_code* code);
+
+/* Sizes of a code; any output pointer may be NULL. */
+gfbp_status gfbp_code_info(const gfbp_code* code, int32_t* q, int32_t* M, int32_t* N, int64_t* E,
+                           int32_t* max_row_degree, int32_t* max_col_degree);
+
+/* ------------------------------------------------------------- decoding */
+typedef enum {
+    GFBP_BSC = 0,    /* obs [F][N][p] bits 0/1; param = flip rate f          */
+    GFBP_BEC = 1,    /* obs [F][N][p] bits 0/1, 2 = erased; param unused      */
+    GFBP_BIAWGN = 2, /* obs [F][N][p] real y, BPSK bit 0 -> +1; param = sigma */
+    GFBP_LOGLIK = 3  /* obs [F][N][q] log-likelihood of every symbol          */
+} gfbp_channel_kind;
+
+typedef struct {
+    int32_t kind;             /* gfbp_channel_kind */
+    float param;              /* f (BSC), sigma (BI-AWGN); ignored otherwise */
+    const float* frame_param; /* optional device [F]: per-frame param (overrides param) */
+} gfbp_channel;
+
+typedef enum { GFBP_PUS = 0, GFBP_SUS = 1 } gfbp_schedule;
+
+typedef enum { GFBP_PRIOR_IID = 0, GFBP_PRIOR_MARKOV = 1 } gfbp_prior_kind;
+
+/*
+ * Source prior (Sec. 2).  I.i.d.: Pr(s = a) = 1/q for every symbol.  Markov:
+ * dynamical block priors re-estimated after every iteration by Eq. 6-7 from
+ * the pseudo-posteriors of the neighbouring source symbols; every other symbol
+ * keeps the uniform prior.
+ */
+typedef struct {
+    int32_t kind;           /* gfbp_prior_kind */
+    const double* T;        /* host [q][q] transition matrix, T[a][b] = Pr(next = b | a);
+                               rows are renormalised to sum 1 */
+    int32_t K;              /* number of source symbols, 1 <= K <= N */
+    const int32_t* src_pos; /* host [K] distinct symbol positions in source order;
+                               NULL = 0..K-1 */
+} gfbp_prior;
+
+/* Optional inputs and outputs of gfbp_decode / gfbp_step (NULL = defaults). */
+typedef struct {
+    const uint8_t* punct;    /* device [N]: 1 = symbol not observed (uniform likelihood) */
+    const uint8_t* syndrome; /* device [F][M]: decode H x = z (Eq. 2); NULL = z = 0 */
+    float* post;             /* device [F][N][q]: pseudo-posteriors Q (Eq. 5) at the end */
+    uint8_t* xhat_trace;     /* device [F][max_iter][N]: hard decisions after every
+                                iteration, 255 after the frame stopped (decode only) */
+    int32_t no_early_stop;   /* nonzero: run max_iter iterations even after H x = z */
+    void* workspace;         /* device scratch of >= gfbp_workspace_size() bytes, 256-byte
+                                aligned; NULL = the library allocates it stream-ordered */
+    size_t workspace_bytes;
+} gfbp_options;
+
+/*
+ * Scratch bytes that gfbp_decode (step = 0) or gfbp_step (step = 1) needs for
+ * n_frames frames with this schedule and prior.
+ */
+gfbp_status gfbp_workspace_size(const gfbp_code* code, int32_t n_frames, gfbp_schedule schedule,
+                                const gfbp_prior* prior, int32_t step, size_t* bytes);
+
+/*
+ * Decode n_frames independent frames (Sec. 2).  Per frame: channel
+ * likelihoods times the source prior give p_j; q_ij <- p_j; then iterations of
+ * the schedule — PUS: every r_ij by Eq. 3 from the previous iteration's q,
+ * then every q_ij and Q_j by Eqs. 4-5; SUS: for j = 0..N-1 in order, r_ij for
+ * the checks of column j from the current q, then q_ij and Q_j of column j —
+ * each followed by the hard decision (argmax of Q_j, lowest symbol on ties)
+ * and the test H x = z; the frame stops at the first iteration that passes or
+ * after max_iter.  With a Markov prior the block priors are re-estimated
+ * (Eq. 6-7) from the finished iteration's Q and used in the next one.
+ *   obs       device, see gfbp_channel_kind.
+ *   max_iter  >= 1.
+ *   x_hat     device [F][N]: decided symbols of the last iteration.
+ *   iters     device [F]: iterations run (1..max_iter).
+ *   converged device [F]: 1 when H x_hat = z.
+ */
+gfbp_status gfbp_decode(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
+                        gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter, uint8_t* x_hat,
+                        int32_t* iters, uint8_t* converged, const gfbp_options* options, void* stream);
+
+/*
+ * Exactly one iteration of the schedule from a caller-supplied state, for
+ * lock-step comparison with a reference.
+ *   msg        device [F][E][q] in/out: q_ij before the iteration; q_ij after it.
+ *   prior_in   device [F][K][q]: block priors used in this iteration (Markov only).
+ *   prior_out  device [F][K][q]: Eq. 6-7 from this iteration's Q (Markov only; may be NULL).
+ *   post       device [F][N][q]: Q_j after the iteration.
+ *   x_hat      device [F][N]; sat device [F]: 1 when H x_hat = z.
+ * options->xhat_trace and no_early_stop are ignored.
+ */
+gfbp_status gfbp_step(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
+                      gfbp_schedule schedule, const gfbp_prior* prior, float* msg, const float* prior_in,
+                      float* prior_out, float* post, uint8_t* x_hat, uint8_t* sat,
+                      const gfbp_options* options, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFBP_H */

@@ -1,0 +1,178 @@
+// Code objects: validation of H, GF(2^p) tables, CSR/CSC index arrays and
+// their single device allocation (Sec. 2: row i of H lists the symbols of
+// check i, column j the checks of symbol j).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "gfbp_internal.cuh"
+
+namespace gfbp {
+void set_error(const std::string& msg);
+}
+
+using gfbp::set_error;
+
+namespace {
+
+uint32_t default_poly(int p) {
+    static const uint32_t polys[9] = {0, 0x3, 0x7, 0xB, 0x13, 0x25, 0x43, 0x89, 0x11D};
+    return (p >= 1 && p <= 8) ? polys[p] : 0;
+}
+
+int log2_exact(int q) {
+    for (int p = 1; p <= 8; p++)
+        if ((1 << p) == q) return p;
+    return -1;
+}
+
+// exp/log tables of the primitive element x; false if poly is not primitive.
+bool build_field(int q, int p, uint32_t poly, uint8_t* ex, uint8_t* lg) {
+    if ((poly >> p) != 1u) return false;
+    std::vector<int> seen(q, -1);
+    uint32_t v = 1;
+    for (int i = 0; i < q - 1; i++) {
+        if (seen[v] != -1) return false;
+        seen[v] = i;
+        ex[i] = (uint8_t)v;
+        lg[v] = (uint8_t)i;
+        v <<= 1;
+        if (v & (uint32_t)q) v ^= poly;
+    }
+    if (v != 1u) return false;
+    for (int i = q - 1; i < 512; i++) ex[i] = ex[i % (q - 1)];
+    lg[0] = 0;
+    return true;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t nnz, const int32_t* row,
+                                        const int32_t* col, const int32_t* val, uint32_t prim_poly,
+                                        gfbp_code** out) {
+    if (!out) { set_error("gfbp_code_create: out is NULL"); return GFBP_EINVAL; }
+    *out = nullptr;
+    const int p = log2_exact(q);
+    if (p < 0) { set_error("gfbp_code_create: q must be 2^p with 1 <= p <= 8"); return GFBP_EINVAL; }
+    if (M < 0 || N < 1 || nnz < 0 || nnz > (int64_t)1 << 31) {
+        set_error("gfbp_code_create: need M >= 0, N >= 1, 0 <= nnz < 2^31");
+        return GFBP_EINVAL;
+    }
+    if (nnz > 0 && (!row || !col || !val)) { set_error("gfbp_code_create: NULL COO array"); return GFBP_EINVAL; }
+    const uint32_t poly = prim_poly ? prim_poly : default_poly(p);
+    uint8_t ex[512] = {0}, lg[256] = {0};
+    if (!build_field(q, p, poly, ex, lg)) {
+        set_error("gfbp_code_create: field polynomial is not primitive of degree log2(q)");
+        return GFBP_EINVAL;
+    }
+    const long long E = nnz;
+    std::vector<long long> order(E);
+    for (long long e = 0; e < E; e++) {
+        if (row[e] < 0 || row[e] >= M || col[e] < 0 || col[e] >= N || val[e] < 1 || val[e] >= q) {
+            set_error("gfbp_code_create: COO entry " + std::to_string(e) + " out of range");
+            return GFBP_EINVAL;
+        }
+        order[e] = e;
+    }
+    std::sort(order.begin(), order.end(), [&](long long a, long long b) {
+        return row[a] != row[b] ? row[a] < row[b] : col[a] < col[b];
+    });
+    std::vector<int> rowptr(M + 1, 0), colptr(N + 1, 0), ecol(E), erow(E), cedge(E);
+    std::vector<uint8_t> eh(E);
+    for (long long k = 0; k < E; k++) {
+        const long long e = order[k];
+        if (k > 0 && row[order[k - 1]] == row[e] && col[order[k - 1]] == col[e]) {
+            set_error("gfbp_code_create: duplicate (row, col) entry");
+            return GFBP_EINVAL;
+        }
+        erow[k] = row[e];
+        ecol[k] = col[e];
+        eh[k] = (uint8_t)val[e];
+        rowptr[row[e] + 1]++;
+        colptr[col[e] + 1]++;
+    }
+    for (int i = 0; i < M; i++) rowptr[i + 1] += rowptr[i];
+    for (int j = 0; j < N; j++) colptr[j + 1] += colptr[j];
+    {
+        std::vector<int> fill(N, 0);
+        for (long long k = 0; k < E; k++) cedge[colptr[ecol[k]] + fill[ecol[k]]++] = (int)k;
+    }
+    int dcmax = 0, dvmax = 0;
+    for (int i = 0; i < M; i++) dcmax = std::max(dcmax, rowptr[i + 1] - rowptr[i]);
+    for (int j = 0; j < N; j++) dvmax = std::max(dvmax, colptr[j + 1] - colptr[j]);
+    if (dcmax > 16 || dvmax > 8) {
+        set_error("gfbp_code_create: row degree must be <= 16 and column degree <= 8");
+        return GFBP_EUNSUPPORTED;
+    }
+
+    // one device allocation: rowptr | colptr | ecol | erow | cedge | eh | gexp | glog
+    size_t off[8], total = 0;
+    const size_t sz[8] = {sizeof(int) * (size_t)(M + 1), sizeof(int) * (size_t)(N + 1), sizeof(int) * (size_t)E,
+                          sizeof(int) * (size_t)E,       sizeof(int) * (size_t)E,       (size_t)E,
+                          512,                           256};
+    for (int k = 0; k < 8; k++) { off[k] = total; total += align256(sz[k] ? sz[k] : 1); }
+    std::vector<uint8_t> host(total, 0);
+    std::memcpy(host.data() + off[0], rowptr.data(), sz[0]);
+    std::memcpy(host.data() + off[1], colptr.data(), sz[1]);
+    if (E) {
+        std::memcpy(host.data() + off[2], ecol.data(), sz[2]);
+        std::memcpy(host.data() + off[3], erow.data(), sz[3]);
+        std::memcpy(host.data() + off[4], cedge.data(), sz[4]);
+        std::memcpy(host.data() + off[5], eh.data(), sz[5]);
+    }
+    std::memcpy(host.data() + off[6], ex, 512);
+    std::memcpy(host.data() + off[7], lg, 256);
+
+    gfbp_code* c = new (std::nothrow) gfbp_code();
+    if (!c) { set_error("gfbp_code_create: out of host memory"); return GFBP_ENOMEM; }
+    cudaError_t err = cudaGetDevice(&c->device);
+    if (err == cudaSuccess) err = cudaMalloc(&c->dmem, total);
+    if (err != cudaSuccess) {
+        set_error(std::string("gfbp_code_create: ") + cudaGetErrorString(err));
+        delete c;
+        return err == cudaErrorMemoryAllocation ? GFBP_ENOMEM : GFBP_ECUDA;
+    }
+    err = cudaMemcpy(c->dmem, host.data(), total, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        set_error(std::string("gfbp_code_create: ") + cudaGetErrorString(err));
+        cudaFree(c->dmem);
+        delete c;
+        return GFBP_ECUDA;
+    }
+    uint8_t* base = static_cast<uint8_t*>(c->dmem);
+    gfbp::CodeDev& d = c->dev;
+    d.q = q; d.p = p; d.M = M; d.N = N; d.E = E; d.dcmax = dcmax; d.dvmax = dvmax;
+    d.rowptr = reinterpret_cast<const int*>(base + off[0]);
+    d.colptr = reinterpret_cast<const int*>(base + off[1]);
+    d.ecol = reinterpret_cast<const int*>(base + off[2]);
+    d.erow = reinterpret_cast<const int*>(base + off[3]);
+    d.cedge = reinterpret_cast<const int*>(base + off[4]);
+    d.eh = base + off[5];
+    d.gexp = base + off[6];
+    d.glog = base + off[7];
+    c->poly = poly;
+    *out = c;
+    return GFBP_OK;
+}
+
+extern "C" void gfbp_code_destroy(gfbp_code* code) {
+    if (!code) return;
+    cudaFree(code->dmem);
+    delete code;
+}
+
+extern "C" gfbp_status gfbp_code_info(const gfbp_code* code, int32_t* q, int32_t* M, int32_t* N, int64_t* E,
+                                      int32_t* max_row_degree, int32_t* max_col_degree) {
+    if (!code) { set_error("gfbp_code_info: NULL code"); return GFBP_EINVAL; }
+    if (q) *q = code->dev.q;
+    if (M) *M = code->dev.M;
+    if (N) *N = code->dev.N;
+    if (E) *E = code->dev.E;
+    if (max_row_degree) *max_row_degree = code->dev.dcmax;
+    if (max_col_degree) *max_col_degree = code->dev.dvmax;
+    return GFBP_OK;
+}

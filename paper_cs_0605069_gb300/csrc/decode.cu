@@ -1,0 +1,397 @@
+// gfbp_decode / gfbp_step: argument checks, workspace layout, the channel
+// likelihood kernel and dispatch to the schedule kernels.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gfbp_internal.cuh"
+
+namespace gfbp {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+constexpr int kChanThreads = 256;
+
+// Channel likelihoods (Sec. 2 and its footnote on other channels), one lane
+// group per symbol, normalised:
+//   BSC:     (1-f)^(p-n) f^n, n = bits where a and the received symbol differ,
+//            formed as r^n with r = f/(1-f) (or the mirror for f > 1/2);
+//   BEC:     1 when a agrees with every non-erased bit (2 = erased), else 0;
+//   BI-AWGN: exp(-sum_k (y_k - s_k(a))^2 / (2 sigma^2)) with BPSK bit 0 -> +1,
+//            formed relative to its maximum: exp(-sum over bits whose sign
+//            disagrees with y_k of 2|y_k|/sigma^2);
+//   LOGLIK:  exp(obs_a - max);
+//   punctured symbols: uniform.
+template <int Q>
+__global__ void __launch_bounds__(kChanThreads) k_channel(const DecodeArgs A) {
+    constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+    constexpr int P = (Q == 2) ? 1 : (Q == 4) ? 2 : (Q == 8) ? 3 : (Q == 16) ? 4 : (Q == 32) ? 5 : (Q == 64) ? 6 : (Q == 128) ? 7 : 8;
+    const int g = threadIdx.x & (G - 1);
+    const unsigned mask = group_mask<G>();
+    const long long groups = (long long)gridDim.x * (blockDim.x / G);
+    const long long total = (long long)A.F * A.c.N;
+    for (long long it = (long long)blockIdx.x * (blockDim.x / G) + threadIdx.x / G; it < total; it += groups) {
+        const int f = (int)(it / A.c.N);
+        const int j = (int)(it % A.c.N);
+        float x[V];
+        const bool punct = A.punct && A.punct[j];
+        const float prm = A.frame_param ? A.frame_param[f] : A.ch_param;
+        if (punct) {
+#pragma unroll
+            for (int v = 0; v < V; v++) x[v] = 1.f;
+        } else if (A.ch_kind == GFBP_LOGLIK) {
+            const float* y = A.obs + (size_t)it * Q;
+            float mx = -INFINITY;
+#pragma unroll
+            for (int v = 0; v < V; v++) { x[v] = y[g * V + v]; mx = fmaxf(mx, x[v]); }
+#pragma unroll
+            for (int m = 1; m < G; m <<= 1) mx = fmaxf(mx, __shfl_xor_sync(mask, mx, m));
+#pragma unroll
+            for (int v = 0; v < V; v++) x[v] = expf(x[v] - mx);
+        } else {
+            const float* y = A.obs + (size_t)it * P;
+            int rx = 0, era = 0;
+            float wgt[P];
+#pragma unroll
+            for (int k = 0; k < P; k++) {
+                const float yk = y[k];
+                if (A.ch_kind == GFBP_BIAWGN) {
+                    rx |= (yk < 0.f) << k;   // bit whose BPSK sign agrees with y_k
+                    wgt[k] = 2.f * fabsf(yk) / (prm * prm);
+                } else {
+                    rx |= (yk > 0.5f && yk < 1.5f) << k;
+                    era |= (yk > 1.5f) << k;
+                    wgt[k] = 0.f;
+                }
+            }
+            if (A.ch_kind == GFBP_BSC) {
+                const bool mirror = prm > 0.5f;
+                const float r = mirror ? (1.f - prm) / prm : prm / (1.f - prm);
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const int n = __popc((g * V + v) ^ rx);
+                    float w = 1.f;
+                    for (int k = 0; k < (mirror ? P - n : n); k++) w *= r;
+                    x[v] = w;
+                }
+            } else if (A.ch_kind == GFBP_BEC) {
+#pragma unroll
+                for (int v = 0; v < V; v++) x[v] = (((g * V + v) ^ rx) & ~era) ? 0.f : 1.f;
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const int dis = (g * V + v) ^ rx;
+                    float s = 0.f;
+#pragma unroll
+                    for (int k = 0; k < P; k++)
+                        if ((dis >> k) & 1) s += wgt[k];
+                    x[v] = expf(-s);
+                }
+            }
+        }
+        gnormalise<Q>(x, mask);
+        stv<V>(A.L + (size_t)it * Q + g * V, x);
+    }
+}
+
+template <int Q>
+cudaError_t launch_channel_q(const DecodeArgs& A, cudaStream_t s) {
+    constexpr int G = Lay<Q>::G;
+    const long long total = (long long)A.F * A.c.N;
+    long long blocks = (total + (kChanThreads / G) - 1) / (kChanThreads / G);
+    if (blocks > 65535LL * 16) blocks = 65535LL * 16;
+    if (blocks < 1) return cudaSuccess;
+    k_channel<Q><<<(unsigned)blocks, kChanThreads, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_channel(const DecodeArgs& A, cudaStream_t s) {
+    switch (A.c.q) {
+    case 2: return launch_channel_q<2>(A, s);
+    case 4: return launch_channel_q<4>(A, s);
+    case 8: return launch_channel_q<8>(A, s);
+    case 16: return launch_channel_q<16>(A, s);
+    case 32: return launch_channel_q<32>(A, s);
+    case 64: return launch_channel_q<64>(A, s);
+    case 128: return launch_channel_q<128>(A, s);
+    case 256: return launch_channel_q<256>(A, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t L, msg, Qsrc, P, Mt, pi, src_index, src_pos, work, total;
+};
+
+Layout layout(const CodeDev& c, long long F, bool markov, int K, bool step) {
+    Layout l{};
+    size_t o = 0;
+    const size_t q = (size_t)c.q;
+    l.work = o; o += 256;
+    l.L = o; o += align256(sizeof(float) * (size_t)F * c.N * q);
+    l.msg = o; o += align256(sizeof(float) * (size_t)F * (size_t)c.E * q);
+    if (markov) {
+        l.Qsrc = o; o += align256(sizeof(float) * (size_t)F * K * q);
+        if (!step) { l.P = o; o += align256(sizeof(float) * (size_t)F * K * q); }
+        l.Mt = o; o += align256(sizeof(float) * q * q);
+        l.pi = o; o += align256(sizeof(float) * q);
+        l.src_index = o; o += align256(sizeof(int) * (size_t)c.N);
+        l.src_pos = o; o += align256(sizeof(int) * (size_t)K);
+    }
+    l.total = o;
+    return l;
+}
+
+int device_sms() {
+    static int sms[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 1;
+    if (!sms[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        sms[dev] = v > 0 ? v : 1;
+    }
+    return sms[dev];
+}
+
+// Stationary distribution of a row-stochastic matrix (pi T = pi, sum 1), by
+// Gaussian elimination with partial pivoting on (T^T - I) with one row
+// replaced by the normalisation.
+bool stationary(const std::vector<double>& T, int q, std::vector<double>& pi) {
+    std::vector<double> A((size_t)q * (q + 1));
+    for (int r = 0; r < q; r++) {
+        for (int c = 0; c < q; c++) A[r * (q + 1) + c] = (r == q - 1) ? 1.0 : T[c * q + r] - (r == c ? 1.0 : 0.0);
+        A[r * (q + 1) + q] = (r == q - 1) ? 1.0 : 0.0;
+    }
+    for (int c = 0; c < q; c++) {
+        int pv = c;
+        for (int r = c + 1; r < q; r++)
+            if (std::fabs(A[r * (q + 1) + c]) > std::fabs(A[pv * (q + 1) + c])) pv = r;
+        if (std::fabs(A[pv * (q + 1) + c]) < 1e-300) return false;
+        if (pv != c)
+            for (int k = 0; k <= q; k++) std::swap(A[c * (q + 1) + k], A[pv * (q + 1) + k]);
+        for (int r = 0; r < q; r++) {
+            if (r == c) continue;
+            const double f = A[r * (q + 1) + c] / A[c * (q + 1) + c];
+            if (f == 0.0) continue;
+            for (int k = c; k <= q; k++) A[r * (q + 1) + k] -= f * A[c * (q + 1) + k];
+        }
+    }
+    pi.assign(q, 0.0);
+    for (int r = 0; r < q; r++) pi[r] = A[r * (q + 1) + q] / A[r * (q + 1) + r];
+    return true;
+}
+
+gfbp_status cuda_fail(const char* where, cudaError_t e) {
+    set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GFBP_ENOMEM : GFBP_ECUDA;
+}
+
+struct Common {
+    bool markov = false;
+    int K = 0;
+    std::vector<float> Mt, pi;
+    std::vector<int> src_index, src_pos;
+};
+
+gfbp_status check_common(const char* fn, const gfbp_code* code, int32_t F, const float* obs, gfbp_channel ch,
+                         gfbp_schedule schedule, const gfbp_prior* prior, Common& C) {
+    const std::string w(fn);
+    if (!code) { set_error(w + ": NULL code"); return GFBP_EINVAL; }
+    if (F < 0) { set_error(w + ": n_frames < 0"); return GFBP_EINVAL; }
+    if (F > 0 && !obs) { set_error(w + ": NULL obs"); return GFBP_EINVAL; }
+    if (ch.kind < GFBP_BSC || ch.kind > GFBP_LOGLIK) { set_error(w + ": unknown channel kind"); return GFBP_EINVAL; }
+    if (!ch.frame_param) {
+        if (ch.kind == GFBP_BSC && !(ch.param > 0.f && ch.param < 1.f)) {
+            set_error(w + ": BSC flip rate must be in (0, 1)");
+            return GFBP_EINVAL;
+        }
+        if (ch.kind == GFBP_BIAWGN && !(ch.param > 0.f && std::isfinite(ch.param))) {
+            set_error(w + ": BI-AWGN sigma must be > 0");
+            return GFBP_EINVAL;
+        }
+    }
+    if (schedule != GFBP_PUS && schedule != GFBP_SUS) { set_error(w + ": unknown schedule"); return GFBP_EINVAL; }
+    const int q = code->dev.q, N = code->dev.N;
+    if (prior && prior->kind == GFBP_PRIOR_MARKOV) {
+        if (!prior->T || prior->K < 1 || prior->K > N) {
+            set_error(w + ": Markov prior needs T and 1 <= K <= N");
+            return GFBP_EINVAL;
+        }
+        C.markov = true;
+        C.K = prior->K;
+        std::vector<double> T((size_t)q * q);
+        for (int a = 0; a < q; a++) {
+            double s = 0.0;
+            for (int b = 0; b < q; b++) {
+                const double t = prior->T[a * q + b];
+                if (!(t >= 0.0) || !std::isfinite(t)) { set_error(w + ": T entries must be finite and >= 0"); return GFBP_EINVAL; }
+                s += t;
+            }
+            if (!(s > 0.0)) { set_error(w + ": T has a zero row"); return GFBP_EINVAL; }
+            for (int b = 0; b < q; b++) T[a * q + b] = prior->T[a * q + b] / s;
+        }
+        std::vector<double> pi;
+        if (!stationary(T, q, pi)) { set_error(w + ": T has no unique stationary distribution"); return GFBP_EINVAL; }
+        C.Mt.assign(T.begin(), T.end());
+        C.pi.assign(pi.begin(), pi.end());
+        C.src_index.assign(N, -1);
+        C.src_pos.resize(C.K);
+        for (int i = 0; i < C.K; i++) {
+            const int j = prior->src_pos ? prior->src_pos[i] : i;
+            if (j < 0 || j >= N || C.src_index[j] != -1) {
+                set_error(w + ": src_pos must hold distinct positions in [0, N)");
+                return GFBP_EINVAL;
+            }
+            C.src_index[j] = i;
+            C.src_pos[i] = j;
+        }
+    } else if (prior && prior->kind != GFBP_PRIOR_IID) {
+        set_error(w + ": unknown prior kind");
+        return GFBP_EINVAL;
+    }
+    return GFBP_OK;
+}
+
+gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel ch, gfbp_schedule schedule,
+                const Common& C, int32_t max_iter, bool step, uint8_t* x_hat, int32_t* iters, uint8_t* conv,
+                float* msg_io, const float* prior_in, float* prior_out, const gfbp_options* opt, void* stream_v) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    const CodeDev& c = code->dev;
+    const Layout l = layout(c, F, C.markov, C.K, step);
+    DecodeArgs A{};
+    A.c = c;
+    A.F = F;
+    A.obs = obs;
+    A.ch_kind = ch.kind;
+    A.ch_param = ch.param;
+    A.frame_param = ch.frame_param;
+    A.punct = opt ? opt->punct : nullptr;
+    A.syn = opt ? opt->syndrome : nullptr;
+    A.max_iter = max_iter;
+    A.early_stop = (opt && opt->no_early_stop && !step) ? 0 : 1;
+    A.markov = C.markov;
+    A.K = C.K;
+    A.xhat = x_hat;
+    A.iters = iters;
+    A.conv = conv;
+    A.post = opt ? opt->post : nullptr;
+    A.trace = (opt && !step) ? opt->xhat_trace : nullptr;
+    A.step = step;
+    A.msg_io = msg_io;
+    A.prior_out = prior_out;
+
+    void* ws = opt ? opt->workspace : nullptr;
+    bool own = false;
+    cudaError_t e = cudaSuccess;
+    if (ws) {
+        if (opt->workspace_bytes < l.total || (reinterpret_cast<uintptr_t>(ws) & 255)) {
+            set_error("workspace too small or not 256-byte aligned");
+            return GFBP_EINVAL;
+        }
+    } else {
+        e = cudaMallocAsync(&ws, l.total, stream);
+        if (e != cudaSuccess) return cuda_fail("workspace allocation", e);
+        own = true;
+    }
+    uint8_t* base = static_cast<uint8_t*>(ws);
+    A.work = reinterpret_cast<int*>(base + l.work);
+    A.L = reinterpret_cast<float*>(base + l.L);
+    A.msg = reinterpret_cast<float*>(base + l.msg);
+    if (C.markov) {
+        A.Qsrc = reinterpret_cast<float*>(base + l.Qsrc);
+        A.P = step ? const_cast<float*>(prior_in) : reinterpret_cast<float*>(base + l.P);
+        float* Mt = reinterpret_cast<float*>(base + l.Mt);
+        float* pi = reinterpret_cast<float*>(base + l.pi);
+        int* sidx = reinterpret_cast<int*>(base + l.src_index);
+        int* spos = reinterpret_cast<int*>(base + l.src_pos);
+        A.Mt = Mt;
+        A.pi = pi;
+        A.src_index = sidx;
+        A.src_pos = spos;
+        const size_t q = (size_t)c.q;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Mt, C.Mt.data(), sizeof(float) * q * q, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pi, C.pi.data(), sizeof(float) * q, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sidx, C.src_index.data(), sizeof(int) * c.N, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(spos, C.src_pos.data(), sizeof(int) * C.K, cudaMemcpyHostToDevice, stream);
+        if (!step) {
+            // initial block priors: the stationary distribution (reading of Sec. 2)
+            std::vector<float> P0((size_t)F * C.K * q);
+            for (size_t k = 0; k < P0.size(); k++) P0[k] = C.pi[k % q];
+            if (e == cudaSuccess && !P0.empty())
+                e = cudaMemcpyAsync(A.P, P0.data(), sizeof(float) * P0.size(), cudaMemcpyHostToDevice, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // P0 is pageable and local
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(A.work, 0, sizeof(int), stream);
+    if (e == cudaSuccess) e = launch_channel(A, stream);
+    if (e == cudaSuccess) e = (schedule == GFBP_PUS) ? launch_pus(A, device_sms(), stream) : launch_sus(A, device_sms(), stream);
+    if (own) {
+        cudaError_t e2 = cudaFreeAsync(ws, stream);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) return cuda_fail("decode launch", e);
+    return GFBP_OK;
+}
+
+}  // namespace
+}  // namespace gfbp
+
+using namespace gfbp;
+
+extern "C" const char* gfbp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" gfbp_status gfbp_workspace_size(const gfbp_code* code, int32_t n_frames, gfbp_schedule schedule,
+                                           const gfbp_prior* prior, int32_t step, size_t* bytes) {
+    if (!code || !bytes || n_frames < 0) { set_error("gfbp_workspace_size: bad argument"); return GFBP_EINVAL; }
+    if (schedule != GFBP_PUS && schedule != GFBP_SUS) { set_error("gfbp_workspace_size: unknown schedule"); return GFBP_EINVAL; }
+    const bool markov = prior && prior->kind == GFBP_PRIOR_MARKOV;
+    *bytes = layout(code->dev, n_frames, markov, markov ? prior->K : 0, step != 0).total;
+    return GFBP_OK;
+}
+
+extern "C" gfbp_status gfbp_decode(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
+                                   gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter, uint8_t* x_hat,
+                                   int32_t* iters, uint8_t* converged, const gfbp_options* options, void* stream) {
+    Common C;
+    gfbp_status st = check_common("gfbp_decode", code, n_frames, obs, channel, schedule, prior, C);
+    if (st != GFBP_OK) return st;
+    if (max_iter < 1) { set_error("gfbp_decode: max_iter must be >= 1"); return GFBP_EINVAL; }
+    if (n_frames > 0 && (!x_hat || !iters || !converged)) { set_error("gfbp_decode: NULL output"); return GFBP_EINVAL; }
+    if (n_frames == 0) return GFBP_OK;
+    return run(code, n_frames, obs, channel, schedule, C, max_iter, false, x_hat, iters, converged, nullptr,
+               nullptr, nullptr, options, stream);
+}
+
+extern "C" gfbp_status gfbp_step(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
+                                 gfbp_schedule schedule, const gfbp_prior* prior, float* msg, const float* prior_in,
+                                 float* prior_out, float* post, uint8_t* x_hat, uint8_t* sat,
+                                 const gfbp_options* options, void* stream) {
+    Common C;
+    gfbp_status st = check_common("gfbp_step", code, n_frames, obs, channel, schedule, prior, C);
+    if (st != GFBP_OK) return st;
+    if (n_frames > 0 && (!msg || !post || !x_hat || !sat)) { set_error("gfbp_step: NULL msg/post/x_hat/sat"); return GFBP_EINVAL; }
+    if (C.markov && n_frames > 0 && !prior_in) { set_error("gfbp_step: Markov prior needs prior_in"); return GFBP_EINVAL; }
+    if (n_frames == 0) return GFBP_OK;
+    gfbp_options o{};
+    if (options) o = *options;
+    o.post = post;
+    o.xhat_trace = nullptr;
+    o.no_early_stop = 0;
+    return run(code, n_frames, obs, channel, schedule, C, 1, true, x_hat, nullptr, sat, msg, prior_in,
+               C.markov ? prior_out : nullptr, &o, stream);
+}

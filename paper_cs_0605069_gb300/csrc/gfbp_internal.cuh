@@ -1,0 +1,313 @@
+// Internal declarations and device building blocks of the gfbp library.
+//
+// Message layout.  A probability vector over GF(q) (q = 2^p) is spread over a
+// "group" of G consecutive lanes of a warp, V = q / G entries per lane: lane g
+// of the group holds entries a = g*V .. g*V+V-1, so a group reads or writes a
+// whole vector as G contiguous V-float chunks (float4 for V >= 4).  The
+// Walsh-Hadamard butterflies over the low log2(V) index bits run inside a
+// lane, those over the high bits with __shfl_xor_sync inside the group.
+//
+// Edge slabs are [frame][edge][q] float32 with edges in (row, col) order, so
+// the d_c vectors of one check are contiguous.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gfbp.h"
+
+namespace gfbp {
+
+// Lanes per vector (G) and entries per lane (V) for field size Q.
+template <int Q>
+struct Lay {
+    static constexpr int V = (Q <= 4) ? Q : ((Q / 32 > 4) ? Q / 32 : 4);
+    static constexpr int G = Q / V;
+    static_assert(V * G == Q && G <= 32, "bad layout");
+};
+
+// Device view of a code: all arrays live in one allocation owned by gfbp_code.
+struct CodeDev {
+    int q, p, M, N;
+    long long E;
+    int dcmax, dvmax;
+    const int* rowptr;   // [M+1]
+    const int* ecol;     // [E] column of each edge
+    const int* erow;     // [E] row of each edge
+    const uint8_t* eh;   // [E] GF value of each edge
+    const int* colptr;   // [N+1]
+    const int* cedge;    // [E] edge ids of each column, rows increasing
+    const uint8_t* gexp; // [512] x^i, extended so that i < 2(q-1) needs no reduction
+    const uint8_t* glog; // [256] log_x(a) for a != 0
+};
+
+struct DecodeArgs {
+    CodeDev c;
+    int F;
+    const float* obs;
+    int ch_kind;
+    float ch_param;
+    const float* frame_param;
+    const uint8_t* punct;
+    const uint8_t* syn;
+    int max_iter;
+    int early_stop;
+    // Markov block priors (Eqs. 6-7)
+    int markov;
+    int K;
+    const float* Mt;       // [q][q] row-normalised transition matrix
+    const float* pi;       // [q] stationary distribution
+    const int* src_pos;    // [K]
+    const int* src_index;  // [N] position -> source index or -1
+    // workspace
+    float* L;              // [F][N][q] normalised channel likelihoods
+    float* msg;            // [F][E][q] edge slab
+    float* Qsrc;           // [F][K][q] posteriors of source symbols (Markov)
+    float* P;              // [F][K][q] block priors in use
+    int* work;             // frame counter for persistent kernels
+    // outputs
+    uint8_t* xhat;
+    int* iters;
+    uint8_t* conv;
+    float* post;
+    uint8_t* trace;
+    // lock-step mode (gfbp_step)
+    int step;
+    float* msg_io;         // [F][E][q] q_ij in (before) and out (after)
+    float* prior_out;      // [F][K][q]
+};
+
+// ---------------------------------------------------------------- helpers
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (G == 32) {
+        return 0xffffffffu;
+    } else {
+        const unsigned lane = threadIdx.x & 31u;
+        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void ldv(float (&x)[V], const float* p) {
+    if constexpr (V == 8) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        const float4 b = *(reinterpret_cast<const float4*>(p) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else if constexpr (V == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    } else if constexpr (V == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(p);
+        x[0] = a.x; x[1] = a.y;
+    } else {
+        x[0] = p[0];
+    }
+}
+
+// Load through the read-only path, for inputs no kernel of the decode writes.
+template <int V>
+__device__ __forceinline__ void ldg_v(float (&x)[V], const float* p) {
+    if constexpr (V == 8) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else if constexpr (V == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    } else if constexpr (V == 2) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+        x[0] = a.x; x[1] = a.y;
+    } else {
+        x[0] = __ldg(p);
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void stv(float* p, const float (&x)[V]) {
+    if constexpr (V == 8) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(x[0], x[1], x[2], x[3]);
+        reinterpret_cast<float4*>(p)[1] = make_float4(x[4], x[5], x[6], x[7]);
+    } else if constexpr (V == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    } else if constexpr (V == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+    } else {
+        p[0] = x[0];
+    }
+}
+
+// Unnormalised Walsh-Hadamard transform of the group's vector, in place.
+template <int Q>
+__device__ __forceinline__ void wht(float (&x)[Lay<Q>::V], unsigned mask, int g) {
+    constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+#pragma unroll
+    for (int h = 1; h < V; h <<= 1) {
+#pragma unroll
+        for (int i = 0; i < V; i++) {
+            if (!(i & h)) {
+                const float a = x[i], b = x[i + h];
+                x[i] = a + b;
+                x[i + h] = a - b;
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 1; m < G; m <<= 1) {
+#pragma unroll
+        for (int i = 0; i < V; i++) {
+            const float o = __shfl_xor_sync(mask, x[i], m);
+            x[i] = (g & m) ? (o - x[i]) : (x[i] + o);
+        }
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ float gsum(const float (&x)[Lay<Q>::V], unsigned mask) {
+    constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < V; i++) s += x[i];
+#pragma unroll
+    for (int m = 1; m < G; m <<= 1) s += __shfl_xor_sync(mask, s, m);
+    return s;
+}
+
+// Scale to sum 1; a zero or non-finite sum gives the uniform vector.
+template <int Q>
+__device__ __forceinline__ void gnormalise(float (&x)[Lay<Q>::V], unsigned mask) {
+    constexpr int V = Lay<Q>::V;
+    const float s = gsum<Q>(x, mask);
+    if (s > 0.f && s <= 3.0e38f) {
+        const float r = 1.0f / s;
+#pragma unroll
+        for (int i = 0; i < V; i++) x[i] *= r;
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; i++) x[i] = 1.0f / Q;
+    }
+}
+
+// Index of the largest entry, lowest index among equal maxima.
+template <int Q>
+__device__ __forceinline__ int gargmax(const float (&x)[Lay<Q>::V], unsigned mask, int g) {
+    constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+    float bv = x[0];
+    int bi = g * V;
+#pragma unroll
+    for (int i = 1; i < V; i++) {
+        if (x[i] > bv) { bv = x[i]; bi = g * V + i; }
+    }
+#pragma unroll
+    for (int m = 1; m < G; m <<= 1) {
+        const float ov = __shfl_xor_sync(mask, bv, m);
+        const int oi = __shfl_xor_sync(mask, bi, m);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    return bi;
+}
+
+__device__ __forceinline__ int gf_mul(const uint8_t* ex, const uint8_t* lg, int a, int b) {
+    return (a && b) ? ex[lg[a] + lg[b]] : 0;
+}
+
+// h^{-1} * b
+template <int Q>
+__device__ __forceinline__ int gf_div(const uint8_t* ex, const uint8_t* lg, int b, int h) {
+    return b ? ex[lg[b] + (Q - 1) - lg[h]] : 0;
+}
+
+// Horizontal-pass epilogue (Eq. 3 through the XOR-convolution theorem):
+// G is the product of the other edges' transforms; s = WHT(G)/q is the
+// distribution of y = sum h_m x_m over the other edges; r[a] = s[z + h a]
+// (GF addition = XOR), negatives from rounding set to 0, normalised.
+template <int Q>
+__device__ __forceinline__ void check_finish(float (&x)[Lay<Q>::V], int h, int z, float* sc, unsigned mask, int g,
+                                             const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+    wht<Q>(x, mask, g);
+#pragma unroll
+    for (int i = 0; i < V; i++) sc[g * V + i] = fmaxf(x[i] * (1.0f / Q), 0.0f);
+    __syncwarp(mask);
+#pragma unroll
+    for (int i = 0; i < V; i++) x[i] = sc[z ^ gf_mul(ex, lg, h, g * V + i)];
+    __syncwarp(mask);
+    gnormalise<Q>(x, mask);
+}
+
+// Vertical-pass epilogue: the distribution of h x for x ~ q (entry b = h a
+// takes q[a]) and its transform, ready for the next horizontal pass.
+template <int Q>
+__device__ __forceinline__ void to_transform(float (&x)[Lay<Q>::V], int h, float* sc, unsigned mask, int g,
+                                             const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+#pragma unroll
+    for (int i = 0; i < V; i++) sc[g * V + i] = x[i];
+    __syncwarp(mask);
+#pragma unroll
+    for (int i = 0; i < V; i++) x[i] = sc[gf_div<Q>(ex, lg, g * V + i, h)];
+    __syncwarp(mask);
+    wht<Q>(x, mask, g);
+}
+
+// p_j: normalised channel likelihood times the block prior of a source symbol.
+template <int Q>
+__device__ __forceinline__ void prior_vec(const DecodeArgs& A, int f, int j, float (&x)[Lay<Q>::V], unsigned mask,
+                                          int g) {
+    constexpr int V = Lay<Q>::V;
+    ldg_v<V>(x, A.L + ((size_t)f * A.c.N + j) * Q + g * V);
+    if (A.markov) {
+        const int si = A.src_index[j];
+        if (si >= 0) {
+            float P[V];
+            ldv<V>(P, A.P + ((size_t)f * A.K + si) * Q + g * V);
+#pragma unroll
+            for (int i = 0; i < V; i++) x[i] *= P[i];
+            gnormalise<Q>(x, mask);
+        }
+    }
+}
+
+// Eq. 7 for source index i of frame f from the stored posteriors Qsrc:
+// P^b = (sum_a Q_{i-1}^a M_ab)(sum_c M_bc Q_{i+1}^c); at the first source
+// symbol pi_b replaces the left factor, at the last one 1 replaces the right.
+template <int Q>
+__device__ __forceinline__ void markov_prior(const DecodeArgs& A, int f, int i, float* out, unsigned mask, int g) {
+    constexpr int V = Lay<Q>::V;
+    const int K = A.K;
+    const float* Qm = (i > 0) ? A.Qsrc + ((size_t)f * K + i - 1) * Q : nullptr;
+    const float* Qp = (i < K - 1) ? A.Qsrc + ((size_t)f * K + i + 1) * Q : nullptr;
+    float P[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        const int b = g * V + v;
+        float left = 0.f, right = 0.f;
+        if (Qm) {
+            for (int a = 0; a < Q; a++) left = fmaf(Qm[a], A.Mt[a * Q + b], left);
+        } else {
+            left = A.pi[b];
+        }
+        if (Qp) {
+            for (int c = 0; c < Q; c++) right = fmaf(A.Mt[b * Q + c], Qp[c], right);
+        } else {
+            right = 1.f;
+        }
+        P[v] = left * right;
+    }
+    gnormalise<Q>(P, mask);
+    stv<V>(out + g * V, P);
+}
+
+// Launchers (one instantiation set per schedule, see pus.cu / sus.cu).
+cudaError_t launch_channel(const DecodeArgs& A, cudaStream_t s);
+cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);
+cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s);
+
+}  // namespace gfbp
+
+struct gfbp_code {
+    gfbp::CodeDev dev;
+    void* dmem;      // the single device allocation behind dev's pointers
+    uint32_t poly;
+    int device;
+};

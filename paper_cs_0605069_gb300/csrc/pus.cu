@@ -1,0 +1,242 @@
+// Parallel updating scheme (PUS, flooding; Sec. 2): one persistent CTA per
+// frame.  Each CTA takes frames from a global counter and runs all of a
+// frame's iterations: horizontal pass (every r_ij from the previous
+// iteration's q, Eq. 3), vertical pass (every q_ij and Q_j, Eqs. 4-5),
+// hard decision and the test H x = z, then the block-prior update (Eqs. 6-7)
+// for a Markov source.  Passes are separated by __syncthreads; no host round
+// trip between iterations.
+//
+// The frame's edge slab is updated in place: the horizontal pass replaces the
+// transforms of q_ij by r_ij (each edge belongs to one check), the vertical
+// pass replaces r_ij by the transform of the new q_ij (each edge belongs to
+// one column).
+#include "gfbp_internal.cuh"
+
+namespace gfbp {
+
+namespace {
+
+constexpr int kPusThreads = 256;
+
+// r_ij for every edge of check i: prefix/suffix products of the other edges'
+// transforms (no division: transforms of probability vectors can be 0).
+template <int Q, int DC>
+__device__ __forceinline__ void pus_check(const DecodeArgs& A, float* slab, int f, int i, float* sc, unsigned mask,
+                                          int g, const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+    const int e0 = A.c.rowptr[i];
+    const int d = A.c.rowptr[i + 1] - e0;
+    const int z = A.syn ? (A.syn[(size_t)f * A.c.M + i] & (Q - 1)) : 0;
+    float S[DC][V];
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = 1.f;
+#pragma unroll
+    for (int k = DC - 1; k >= 0; k--) {
+        if (k < d) {
+#pragma unroll
+            for (int v = 0; v < V; v++) S[k][v] = acc[v];
+            float Fk[V];
+            ldv<V>(Fk, slab + (size_t)(e0 + k) * Q + g * V);
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] *= Fk[v];
+        }
+    }
+    float pre[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) pre[v] = 1.f;
+#pragma unroll
+    for (int k = 0; k < DC; k++) {
+        if (k < d) {
+            float Fk[V], x[V];
+            ldv<V>(Fk, slab + (size_t)(e0 + k) * Q + g * V);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                x[v] = pre[v] * S[k][v];
+                pre[v] *= Fk[v];
+            }
+            check_finish<Q>(x, A.c.eh[e0 + k], z, sc, mask, g, ex, lg);
+            stv<V>(slab + (size_t)(e0 + k) * Q + g * V, x);
+        }
+    }
+}
+
+// q_ij for every edge of column j (Eq. 4), Q_j (Eq. 5) and its hard decision.
+template <int Q, int DV>
+__device__ __forceinline__ void pus_var(const DecodeArgs& A, float* slab, int f, int j, float* sc, unsigned mask,
+                                        int g, const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+    const int c0 = A.c.colptr[j];
+    const int d = A.c.colptr[j + 1] - c0;
+    float p[V];
+    prior_vec<Q>(A, f, j, p, mask, g);
+    float S[DV][V];
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = 1.f;
+#pragma unroll
+    for (int k = DV - 1; k >= 0; k--) {
+        if (k < d) {
+#pragma unroll
+            for (int v = 0; v < V; v++) S[k][v] = acc[v];
+            float R[V];
+            ldv<V>(R, slab + (size_t)A.c.cedge[c0 + k] * Q + g * V);
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] *= R[v];
+        }
+    }
+    // pseudo-posterior and hard decision
+    {
+        float Qj[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) Qj[v] = p[v] * acc[v];
+        gnormalise<Q>(Qj, mask);
+        const int a = gargmax<Q>(Qj, mask, g);
+        if (g == 0) A.xhat[(size_t)f * A.c.N + j] = (uint8_t)a;
+        if (A.post) stv<V>(A.post + ((size_t)f * A.c.N + j) * Q + g * V, Qj);
+        if (A.markov) {
+            const int si = A.src_index[j];
+            if (si >= 0) stv<V>(A.Qsrc + ((size_t)f * A.K + si) * Q + g * V, Qj);
+        }
+    }
+    float pre[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) pre[v] = 1.f;
+#pragma unroll
+    for (int k = 0; k < DV; k++) {
+        if (k < d) {
+            const int e = A.c.cedge[c0 + k];
+            float R[V], x[V];
+            ldv<V>(R, slab + (size_t)e * Q + g * V);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                x[v] = p[v] * (pre[v] * S[k][v]);
+                pre[v] *= R[v];
+            }
+            gnormalise<Q>(x, mask);
+            if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + e) * Q + g * V, x);
+            to_transform<Q>(x, A.c.eh[e], sc, mask, g, ex, lg);
+            stv<V>(slab + (size_t)e * Q + g * V, x);
+        }
+    }
+}
+
+template <int Q, int DC, int DV>
+__global__ void __launch_bounds__(kPusThreads) k_pus(const DecodeArgs A) {
+    constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+    __shared__ uint8_t s_exp[512];
+    __shared__ uint8_t s_log[256];
+    __shared__ __align__(16) float s_scr[kPusThreads * V];
+    __shared__ int s_frame;
+
+    const int tid = threadIdx.x;
+    const int g = tid & (G - 1);
+    const int grp = tid / G;
+    const int ngrp = blockDim.x / G;
+    const unsigned mask = group_mask<G>();
+    float* sc = s_scr + grp * Q;
+    for (int k = tid; k < 512; k += blockDim.x) s_exp[k] = A.c.gexp[k];
+    for (int k = tid; k < 256; k += blockDim.x) s_log[k] = A.c.glog[k];
+    const int M = A.c.M, N = A.c.N;
+    const long long E = A.c.E;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_frame = atomicAdd(A.work, 1);
+        __syncthreads();
+        const int f = s_frame;
+        if (f >= A.F) break;
+        float* slab = A.msg + (size_t)f * E * Q;
+
+        // q_ij <- p_j (Sec. 2) or the caller's state, stored as transforms
+        for (long long e = grp; e < E; e += ngrp) {
+            float x[V];
+            if (A.step) {
+                ldv<V>(x, A.msg_io + ((size_t)f * E + e) * Q + g * V);
+            } else {
+                prior_vec<Q>(A, f, A.c.ecol[e], x, mask, g);
+            }
+            to_transform<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+            stv<V>(slab + (size_t)e * Q + g * V, x);
+        }
+        __syncthreads();
+
+        int t = 1, ok = 0;
+        for (;; t++) {
+            for (int i = grp; i < M; i += ngrp) pus_check<Q, DC>(A, slab, f, i, sc, mask, g, s_exp, s_log);
+            __syncthreads();
+            for (int j = grp; j < N; j += ngrp) pus_var<Q, DV>(A, slab, f, j, sc, mask, g, s_exp, s_log);
+            __syncthreads();
+            int bad = 0;
+            for (int i = tid; i < M; i += blockDim.x) {
+                int s = 0;
+                for (int e = A.c.rowptr[i]; e < A.c.rowptr[i + 1]; e++)
+                    s ^= gf_mul(s_exp, s_log, A.c.eh[e], A.xhat[(size_t)f * N + A.c.ecol[e]]);
+                const int z = A.syn ? (A.syn[(size_t)f * M + i] & (Q - 1)) : 0;
+                bad |= (s != z);
+            }
+            ok = !__syncthreads_or(bad);
+            if (A.trace) {
+                uint8_t* tr = A.trace + ((size_t)f * A.max_iter + (t - 1)) * N;
+                for (int j = tid; j < N; j += blockDim.x) tr[j] = A.xhat[(size_t)f * N + j];
+            }
+            if ((ok && A.early_stop) || t >= A.max_iter) break;
+            if (A.markov) {
+                for (int i = grp; i < A.K; i += ngrp)
+                    markov_prior<Q>(A, f, i, A.P + ((size_t)f * A.K + i) * Q, mask, g);
+                __syncthreads();
+            }
+        }
+        if (A.step && A.markov && A.prior_out) {
+            for (int i = grp; i < A.K; i += ngrp)
+                markov_prior<Q>(A, f, i, A.prior_out + ((size_t)f * A.K + i) * Q, mask, g);
+        }
+        if (A.trace) {
+            for (size_t o = (size_t)t * N + tid; o < (size_t)A.max_iter * N; o += blockDim.x)
+                A.trace[(size_t)f * A.max_iter * N + o] = 255;
+        }
+        if (tid == 0) {
+            if (A.iters) A.iters[f] = t;
+            A.conv[f] = (uint8_t)ok;
+        }
+    }
+}
+
+template <int Q, int DC, int DV>
+cudaError_t launch_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    static int occ = -1;
+    if (occ < 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus<Q, DC, DV>, kPusThreads, 0);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+    }
+    long long grid = (long long)num_sms * occ;
+    if (grid > A.F) grid = A.F;
+    if (grid < 1) return cudaSuccess;
+    k_pus<Q, DC, DV><<<(int)grid, kPusThreads, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t launch_deg(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    if (A.c.dcmax <= 6 && A.c.dvmax <= 3) return launch_q<Q, 6, 3>(A, num_sms, s);
+    return launch_q<Q, 16, 8>(A, num_sms, s);
+}
+
+}  // namespace
+
+cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    switch (A.c.q) {
+    case 2: return launch_deg<2>(A, num_sms, s);
+    case 4: return launch_deg<4>(A, num_sms, s);
+    case 8: return launch_deg<8>(A, num_sms, s);
+    case 16: return launch_deg<16>(A, num_sms, s);
+    case 32: return launch_deg<32>(A, num_sms, s);
+    case 64: return launch_deg<64>(A, num_sms, s);
+    case 128: return launch_deg<128>(A, num_sms, s);
+    case 256: return launch_deg<256>(A, num_sms, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gfbp

@@ -1,0 +1,197 @@
+"""Python binding of the gfbp C ABI (include/gfbp.h).
+
+Argument marshalling only: every step of decoding runs in the CUDA library
+libgfbp.so.  PyTorch supplies device memory (CUDA tensors, whose raw
+pointers are passed) and the current stream.  If the library is missing the
+import of this module's functions fails loudly; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgfbp.so")
+_lib = None
+_lock = threading.Lock()
+
+GFBP_OK, GFBP_EINVAL, GFBP_ENOMEM, GFBP_ECUDA, GFBP_ETIMEOUT, GFBP_EBUSY, GFBP_EUNSUPPORTED = range(7)
+CHANNEL = {"bsc": 0, "bec": 1, "awgn": 2, "biawgn": 2, "loglik": 3}
+SCHEDULE = {"pus": 0, "sus": 1}
+
+# Functions declared in include/gfbp.h (the CPU test checks that every one is exported).
+EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info",
+           "gfbp_workspace_size", "gfbp_decode", "gfbp_step")
+
+
+class GfbpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: status {status}: {last_error()}")
+
+
+class gfbp_channel(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("param", C.c_float), ("frame_param", C.c_void_p)]
+
+
+class gfbp_prior(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("T", C.c_void_p), ("K", C.c_int32), ("src_pos", C.c_void_p)]
+
+
+class gfbp_options(C.Structure):
+    _fields_ = [("punct", C.c_void_p), ("syndrome", C.c_void_p), ("post", C.c_void_p),
+                ("xhat_trace", C.c_void_p), ("no_early_stop", C.c_int32), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
+
+
+def lib() -> C.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_cs_0605069_gb300/build.py (no CPU fallback)")
+            L = C.CDLL(LIB_PATH)
+            P, i32, i64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+            L.gfbp_last_error.restype = C.c_char_p
+            L.gfbp_last_error.argtypes = []
+            L.gfbp_code_create.argtypes = [i32, i32, i32, i64, P, P, P, u32, C.POINTER(C.c_void_p)]
+            L.gfbp_code_destroy.argtypes = [P]
+            L.gfbp_code_destroy.restype = None
+            L.gfbp_code_info.argtypes = [P] + [C.POINTER(i32)] * 3 + [C.POINTER(i64)] + [C.POINTER(i32)] * 2
+            L.gfbp_workspace_size.argtypes = [P, i32, i32, C.POINTER(gfbp_prior), i32, C.POINTER(C.c_size_t)]
+            L.gfbp_decode.argtypes = [P, i32, P, gfbp_channel, i32, C.POINTER(gfbp_prior), i32, P, P, P,
+                                      C.POINTER(gfbp_options), P]
+            L.gfbp_step.argtypes = [P, i32, P, gfbp_channel, i32, C.POINTER(gfbp_prior), P, P, P, P, P, P,
+                                    C.POINTER(gfbp_options), P]
+            for fn in ("gfbp_code_create", "gfbp_code_info", "gfbp_workspace_size", "gfbp_decode", "gfbp_step"):
+                getattr(L, fn).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return (lib().gfbp_last_error() or b"").decode()
+
+
+def _ok(rc: int, where: str):
+    if rc != GFBP_OK:
+        raise GfbpError(rc, where)
+
+
+class Code:
+    """A parity-check matrix H over GF(q) on the current CUDA device (gfbp_code_create)."""
+
+    def __init__(self, q: int, M: int, N: int, rows, cols, vals, poly: int = 0):
+        r = np.ascontiguousarray(rows, dtype=np.int32)
+        c = np.ascontiguousarray(cols, dtype=np.int32)
+        v = np.ascontiguousarray(vals, dtype=np.int32)
+        h = C.c_void_p()
+        _ok(lib().gfbp_code_create(int(q), int(M), int(N), int(r.size), r.ctypes.data, c.ctypes.data,
+                                   v.ctypes.data, int(poly), C.byref(h)), "gfbp_code_create")
+        self.handle = h
+        vals_ = [C.c_int32() for _ in range(3)]
+        E = C.c_int64()
+        dc, dv = C.c_int32(), C.c_int32()
+        _ok(lib().gfbp_code_info(h, C.byref(vals_[0]), C.byref(vals_[1]), C.byref(vals_[2]), C.byref(E),
+                                 C.byref(dc), C.byref(dv)), "gfbp_code_info")
+        self.q, self.M, self.N = (x.value for x in vals_)
+        self.E, self.max_row_degree, self.max_col_degree = E.value, dc.value, dv.value
+
+    @classmethod
+    def from_coo(cls, code) -> "Code":
+        """From any object with q, M, N, rows, cols, vals (and optionally poly)."""
+        return cls(code.q, code.M, code.N, code.rows, code.cols, code.vals, getattr(code, "poly", 0) or 0)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().gfbp_code_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _prior(T, K, src_pos):
+    if T is None:
+        return gfbp_prior(0, None, 0, None), None
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    sp = None if src_pos is None else np.ascontiguousarray(src_pos, dtype=np.int32)
+    pr = gfbp_prior(1, T.ctypes.data, int(K), None if sp is None else sp.ctypes.data)
+    return pr, (T, sp)
+
+
+def workspace_size(code: Code, n_frames: int, schedule: str = "pus", T=None, K: int = 0, src_pos=None,
+                   step: bool = False) -> int:
+    pr, _keep = _prior(T, K, src_pos)
+    n = C.c_size_t()
+    _ok(lib().gfbp_workspace_size(code.handle, int(n_frames), SCHEDULE[schedule], C.byref(pr), int(step),
+                                  C.byref(n)), "gfbp_workspace_size")
+    return n.value
+
+
+def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: str = "pus", max_iter: int = 100,
+           T=None, K: int = 0, src_pos=None, frame_param=None, punct=None, syndrome=None, post: bool = False,
+           trace: bool = False, no_early_stop: bool = False, workspace=None, out=None, stream=None):
+    """gfbp_decode on CUDA tensors.  obs: float32 [F][N][p] (or [F][N][q] for
+    loglik).  Returns dict of device tensors x_hat [F][N] uint8, iters [F]
+    int32, converged [F] uint8 (+ post [F][N][q], trace [F][max_iter][N])."""
+    import torch
+    F = int(obs.shape[0])
+    dev = obs.device
+    if out is None:
+        out = dict(x_hat=torch.empty((F, code.N), dtype=torch.uint8, device=dev),
+                   iters=torch.empty(F, dtype=torch.int32, device=dev),
+                   converged=torch.empty(F, dtype=torch.uint8, device=dev))
+        if post:
+            out["post"] = torch.empty((F, code.N, code.q), dtype=torch.float32, device=dev)
+        if trace:
+            out["trace"] = torch.empty((F, max_iter, code.N), dtype=torch.uint8, device=dev)
+    pr, _keep = _prior(T, K, src_pos)
+    if workspace is None:
+        nbytes = workspace_size(code, F, schedule, T, K, src_pos)
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    opt = gfbp_options(_ptr(punct), _ptr(syndrome), _ptr(out.get("post")), _ptr(out.get("trace")),
+                       int(no_early_stop), _ptr(workspace), int(workspace.numel()))
+    ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
+    _ok(lib().gfbp_decode(code.handle, F, _ptr(obs), ch, SCHEDULE[schedule], C.byref(pr), int(max_iter),
+                          _ptr(out["x_hat"]), _ptr(out["iters"]), _ptr(out["converged"]), C.byref(opt),
+                          _stream(stream)), "gfbp_decode")
+    return out
+
+
+def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedule: str = "pus", T=None, K: int = 0,
+         src_pos=None, prior_in=None, frame_param=None, punct=None, syndrome=None, stream=None):
+    """gfbp_step: one iteration from msg (float32 [F][E][q], updated in place).
+    Returns dict(msg, post, x_hat, sat, prior_out)."""
+    import torch
+    F = int(obs.shape[0])
+    dev = obs.device
+    post = torch.empty((F, code.N, code.q), dtype=torch.float32, device=dev)
+    x_hat = torch.empty((F, code.N), dtype=torch.uint8, device=dev)
+    sat = torch.empty(F, dtype=torch.uint8, device=dev)
+    prior_out = torch.empty((F, K, code.q), dtype=torch.float32, device=dev) if T is not None else None
+    pr, _keep = _prior(T, K, src_pos)
+    ws = torch.empty(workspace_size(code, F, schedule, T, K, src_pos, step=True), dtype=torch.uint8, device=dev)
+    opt = gfbp_options(_ptr(punct), _ptr(syndrome), None, None, 0, _ptr(ws), int(ws.numel()))
+    ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
+    _ok(lib().gfbp_step(code.handle, F, _ptr(obs), ch, SCHEDULE[schedule], C.byref(pr), _ptr(msg), _ptr(prior_in),
+                        _ptr(prior_out), _ptr(post), _ptr(x_hat), _ptr(sat), C.byref(opt), _stream(stream)),
+        "gfbp_step")
+    return dict(msg=msg, post=post, x_hat=x_hat, sat=sat, prior_out=prior_out)

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Lock-step: from the oracle's message state at iteration t, one device
+iteration must give the oracle's Q (Eq. 5), q (Eq. 4) and block priors
+(Eqs. 6-7) within LOCKSTEP_ATOL max-abs.  Free-running: decided symbols,
+iteration counts and converged flags identical on every frame except tie
+frames, whose every disagreement sits on a symbol with oracle top-two gap
+<= TIE_GAP (counted and reported).
+"""
+import numpy as np
+import pytest
+
+from tests.parity_util import LOCKSTEP_ATOL, TIE_GAP, classify_frames, gpu_decode, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_cs_0605069_gb300 import gfbp
+    gfbp.lib()
+    return torch
+
+
+def _workload(name, frames, N=None):
+    from paper_cs_0605069_gb300 import workload as W
+    return W.make_batch(name, frames=frames, N=N)
+
+
+def _lockstep(torch_cuda, oracle, code, obs, kind, param, schedule, iters, T=None, K=0, atol=LOCKSTEP_ATOL):
+    import torch
+    from paper_cs_0605069_gb300 import gfbp
+    cd = gfbp.Code.from_coo(code)
+    F = obs.shape[0]
+    msg = oracle.initial_messages(code, obs, kind, param, T=T, K=K)
+    prior = None
+    if T is not None:
+        _, pi = oracle.markov(T, np.full((1, code.q), 1.0 / code.q))
+        prior = np.broadcast_to(pi, (F, K, code.q)).copy()
+    fp = to_dev(np.broadcast_to(np.asarray(param, np.float32), (F,)).copy())
+    worst = 0.0
+    for t in range(iters):
+        ref = oracle.step(code, obs, kind, param, msg, schedule, T=T, K=K, prior=prior)
+        m = to_dev(msg.astype(np.float32))
+        out = gfbp.step(cd, to_dev(obs, torch.float32), m, channel=kind, schedule=schedule, T=T, K=K,
+                        prior_in=None if prior is None else to_dev(prior.astype(np.float32)), frame_param=fp)
+        torch.cuda.synchronize()
+        post = out["post"].cpu().numpy()
+        dpost = np.abs(post - ref["post"]).max()
+        dmsg = np.abs(out["msg"].cpu().numpy() - ref["msg"]).max()
+        worst = max(worst, dpost, dmsg)
+        assert dpost <= atol, f"iteration {t + 1}: Q max-abs {dpost}"
+        assert dmsg <= atol, f"iteration {t + 1}: q max-abs {dmsg}"
+        # hard decisions agree wherever the oracle's decision is not a near tie
+        srt = np.sort(ref["post"], axis=2)
+        gap = srt[..., -1] - srt[..., -2]
+        xh = out["x_hat"].cpu().numpy()
+        firm = gap > TIE_GAP
+        assert (xh[firm] == ref["xhat"][firm]).all()
+        if T is not None:
+            dP = np.abs(out["prior_out"].cpu().numpy() - ref["prior_out"]).max()
+            assert dP <= atol, f"iteration {t + 1}: block prior max-abs {dP}"
+            prior = ref["prior_out"]
+        msg = ref["msg"]
+    return worst
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_lockstep_gf4_n96_bsc(torch_cuda, oracle, schedule):
+    b = _workload("gf4_n96_bsc005", 64)
+    _lockstep(torch_cuda, oracle, b.code, b.obs, "bsc", b.param, schedule, iters=8)
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_lockstep_gf16_n1000_awgn(torch_cuda, oracle, schedule):
+    b = _workload("gf16_n1000_awgn", 12)
+    _lockstep(torch_cuda, oracle, b.code, b.obs, "awgn", b.param, schedule, iters=6)
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_lockstep_gf8_markov(torch_cuda, oracle, schedule):
+    b = _workload("gf8_n2000_markov_bsc", 6, N=400)
+    _lockstep(torch_cuda, oracle, b.code, b.obs, "bsc", b.param, schedule, iters=5, T=b.T, K=b.K)
+
+
+def _free_running(oracle, b, kind, schedule, frames_ok=0.0):
+    from paper_cs_0605069_gb300 import gfbp
+    cd = gfbp.Code.from_coo(b.code)
+    T = b.T
+    K = b.K
+    ora = oracle.decode(b.code, b.obs, kind, b.param, schedule, max_iter=b.max_iter, T=T, K=K, trace=True)
+    gpu = gpu_decode(cd, b.obs, kind, b.param, schedule, b.max_iter, T=T, K=K, trace=True)
+    kinds = classify_frames(gpu, ora)
+    n_fail = int((kinds == "fail").sum())
+    n_tie = int((kinds == "tie").sum())
+    print(f"{schedule}: frames {len(kinds)} match {int((kinds == 'match').sum())} tie {n_tie} fail {n_fail}")
+    assert n_fail == 0, np.nonzero(kinds == "fail")[0][:10]
+    return kinds
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_free_running_gf4_n96_bsc_1000_frames(torch_cuda, oracle, schedule):
+    _free_running(oracle, _workload("gf4_n96_bsc005", 1000), "bsc", schedule)
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_free_running_gf16_n1000_awgn(torch_cuda, oracle, schedule):
+    _free_running(oracle, _workload("gf16_n1000_awgn", 96), "awgn", schedule)
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_free_running_gf8_markov_bsc(torch_cuda, oracle, schedule):
+    _free_running(oracle, _workload("gf8_n2000_markov_bsc", 24), "bsc", schedule)
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_free_running_gf8_markov_bec(torch_cuda, oracle, schedule):
+    _free_running(oracle, _workload("gf8_n2000_markov_bec", 24), "bec", schedule)
+
+
+# ---------------------------------------------------------------- edge cases
+def _tiny_codes():
+    from tests.test_oracle_decoder import chain_code, random_tree_code
+    rng = np.random.default_rng(11)
+    yield "tree-q8", random_tree_code(rng, 6, 8)
+    yield "tree-q2", random_tree_code(rng, 11, 2)
+    yield "chain-q4", chain_code(7, 4, rng)
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_tree_codes_exact_marginals_on_gpu(torch_cuda, oracle, schedule):
+    """Cycle-free graphs: the device reaches the exact marginals (enumeration)
+    and the oracle's posteriors, with a non-zero syndrome."""
+    from paper_cs_0605069_gb300 import gfbp
+    from tests.test_oracle_decoder import exact_marginals
+    for name, code in _tiny_codes():
+        rng = np.random.default_rng(len(name))
+        ll = rng.normal(0, 1.5, size=(3, code.N, code.q)).astype(np.float32)
+        z = rng.integers(0, code.q, size=(3, code.M)).astype(np.uint8)
+        it = code.N + code.M + 2
+        ora = oracle.decode(code, ll, "loglik", 0.0, schedule, max_iter=it, syn=z, early_stop=False, post=True)
+        gpu = gpu_decode(gfbp.Code.from_coo(code), ll, "loglik", 0.0, schedule, it, syndrome=z, post=True,
+                         no_early_stop=True)
+        for f in range(3):
+            L = oracle.channel(code.q, "loglik", 0.0, ll[f])
+            want = exact_marginals(code, L, z[f])
+            np.testing.assert_allclose(gpu["post"][f], want, atol=2e-6)
+            np.testing.assert_allclose(gpu["post"][f], ora["post"][f], atol=2e-6)
+
+
+@pytest.mark.parametrize("q", [2, 32, 64, 128, 256])
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_other_field_sizes(torch_cuda, oracle, q, schedule):
+    """Every field size the library instantiates, on a small regular code
+    over the BI-AWGN channel: lock-step Q and q from the oracle's state."""
+    from paper_cs_0605069_gb300 import workload as W
+    code = W.regular_code(q, 48, cfg=f"fields{q}")
+    rng = np.random.default_rng(q)
+    x = W.encode(code, rng.integers(0, q, size=(4, code.K)))
+    obs = W.biawgn(rng, x, code.p, 0.8)
+    _lockstep(torch_cuda, oracle, code, obs, "awgn", 0.8, schedule, iters=3)
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_irregular_code_generic_kernel(torch_cuda, oracle, schedule):
+    """Row degrees up to 16 and column degrees up to 8 use the generic kernel."""
+    rng = np.random.default_rng(3)
+    q, M, N = 8, 30, 40
+    H = np.zeros((M, N), np.int64)
+    for j in range(N):
+        dv = int(rng.integers(1, 8))
+        for i in rng.choice(np.arange(1, M), size=dv, replace=False):
+            H[i, j] = rng.integers(1, q)
+    H[0, :16] = rng.integers(1, q, size=16)
+    from paper_cs_0605069_gb300 import workload as W
+    code = W.code_from_dense(H, q)
+    assert max(np.bincount(code.rows)) <= 16 and max(np.bincount(code.cols)) <= 8
+    obs = rng.integers(0, 2, size=(5, N, 3)).astype(np.float32)
+    _lockstep(torch_cuda, oracle, code, obs, "bsc", 0.07, schedule, iters=4)
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_punctured_symbols_and_syndrome_form(torch_cuda, oracle, schedule):
+    """MN-style input (Eq. 2): punctured symbols and a non-zero syndrome."""
+    from paper_cs_0605069_gb300 import gfbp
+    b = _workload("gf4_n96_bsc005", 40)
+    code = b.code
+    rng = np.random.default_rng(9)
+    v = rng.integers(0, code.q, size=(40, code.N))
+    z = code.syndrome(v).astype(np.uint8)
+    punct = np.zeros(code.N, np.uint8)
+    punct[:10] = 1
+    obs = (b.obs.astype(np.int64) ^ rng.integers(0, 2, size=b.obs.shape)).astype(np.float32)
+    ora = oracle.decode(code, obs, "bsc", 0.05, schedule, max_iter=40, punct=punct, syn=z, trace=True)
+    gpu = gpu_decode(gfbp.Code.from_coo(code), obs, "bsc", 0.05, schedule, 40, punct=punct, syndrome=z, trace=True)
+    kinds = classify_frames(gpu, ora)
+    assert (kinds != "fail").all()
+
+
+def test_empty_batch_and_errors(torch_cuda):
+    import torch
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch("gf4_n96_bsc005", frames=1)
+    cd = gfbp.Code.from_coo(b.code)
+    out = gfbp.decode(cd, torch.empty((0, b.code.N, 2), device="cuda"), "bsc", 0.05)
+    assert out["x_hat"].shape == (0, b.code.N)
+    with pytest.raises(gfbp.GfbpError) as e:
+        gfbp.decode(cd, to_dev(b.obs), "bsc", 1.5)
+    assert e.value.status == gfbp.GFBP_EINVAL and "flip rate" in str(e.value)
+    with pytest.raises(gfbp.GfbpError):
+        gfbp.decode(cd, to_dev(b.obs), "bsc", 0.05, max_iter=0)
+    with pytest.raises(gfbp.GfbpError):
+        gfbp.decode(cd, to_dev(b.obs), "bsc", 0.05, T=np.eye(4), K=0)
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_single_frame_and_large_batch_agree(torch_cuda, schedule):
+    """A frame decodes to the same bits alone and inside a batch (frames are
+    independent; the persistent kernels take them in any order)."""
+    from paper_cs_0605069_gb300 import gfbp
+    b = _workload("gf16_n1000_awgn", 300)
+    cd = gfbp.Code.from_coo(b.code)
+    full = gpu_decode(cd, b.obs, "awgn", b.param, schedule, 50, post=True)
+    for f in (0, 1, 157, 299):
+        one = gpu_decode(cd, b.obs[f:f + 1], "awgn", b.param[f:f + 1], schedule, 50, post=True)
+        assert one["iters"][0] == full["iters"][f]
+        np.testing.assert_array_equal(one["x_hat"][0], full["x_hat"][f])
+        np.testing.assert_array_equal(one["post"][0], full["post"][f])
