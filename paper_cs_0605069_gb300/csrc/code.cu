@@ -109,12 +109,28 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
         return GFBP_EUNSUPPORTED;
     }
 
-    // one device allocation: rowptr | colptr | ecol | erow | cedge | eh | gexp | glog
-    size_t off[8], total = 0;
-    const size_t sz[8] = {sizeof(int) * (size_t)(M + 1), sizeof(int) * (size_t)(N + 1), sizeof(int) * (size_t)E,
-                          sizeof(int) * (size_t)E,       sizeof(int) * (size_t)E,       (size_t)E,
-                          512,                           256};
-    for (int k = 0; k < 8; k++) { off[k] = total; total += align256(sz[k] ? sz[k] : 1); }
+    // per column slot: {edge, row start, row degree | h << 8, row}; and whether
+    // column j shares a check with column j-1 (SUS prefetch must then reload)
+    std::vector<int4> cinfo(E);
+    std::vector<uint8_t> cdep(N, 0);
+    for (int j = 0; j < N; j++) {
+        for (int k = colptr[j]; k < colptr[j + 1]; k++) {
+            const int e = cedge[k], i = erow[e];
+            cinfo[k] = make_int4(e, rowptr[i], (rowptr[i + 1] - rowptr[i]) | ((int)eh[e] << 8), i);
+            if (j > 0)
+                for (int k2 = colptr[j - 1]; k2 < colptr[j]; k2++)
+                    if (erow[cedge[k2]] == i) cdep[j] = 1;
+        }
+    }
+
+    // one device allocation: rowptr | colptr | ecol | erow | cedge | eh | gexp | glog | cinfo | cdep
+    constexpr int NA = 10;
+    size_t off[NA], total = 0;
+    const size_t sz[NA] = {sizeof(int) * (size_t)(M + 1), sizeof(int) * (size_t)(N + 1), sizeof(int) * (size_t)E,
+                           sizeof(int) * (size_t)E,       sizeof(int) * (size_t)E,       (size_t)E,
+                           512,                           256,                           sizeof(int4) * (size_t)E,
+                           (size_t)N};
+    for (int k = 0; k < NA; k++) { off[k] = total; total += align256(sz[k] ? sz[k] : 1); }
     std::vector<uint8_t> host(total, 0);
     std::memcpy(host.data() + off[0], rowptr.data(), sz[0]);
     std::memcpy(host.data() + off[1], colptr.data(), sz[1]);
@@ -123,9 +139,11 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
         std::memcpy(host.data() + off[3], erow.data(), sz[3]);
         std::memcpy(host.data() + off[4], cedge.data(), sz[4]);
         std::memcpy(host.data() + off[5], eh.data(), sz[5]);
+        std::memcpy(host.data() + off[8], cinfo.data(), sz[8]);
     }
     std::memcpy(host.data() + off[6], ex, 512);
     std::memcpy(host.data() + off[7], lg, 256);
+    std::memcpy(host.data() + off[9], cdep.data(), sz[9]);
 
     gfbp_code* c = new (std::nothrow) gfbp_code();
     if (!c) { set_error("gfbp_code_create: out of host memory"); return GFBP_ENOMEM; }
@@ -154,6 +172,8 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     d.eh = base + off[5];
     d.gexp = base + off[6];
     d.glog = base + off[7];
+    d.cinfo = reinterpret_cast<const int4*>(base + off[8]);
+    d.cdep = base + off[9];
     c->poly = poly;
     *out = c;
     return GFBP_OK;

@@ -339,6 +339,7 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(A.work, 0, sizeof(int), stream);
     if (e == cudaSuccess) e = launch_channel(A, stream);
+    if (e == cudaSuccess && schedule == GFBP_SUS) e = launch_init_dev(A, stream);
     if (e == cudaSuccess) e = (schedule == GFBP_PUS) ? launch_pus(A, device_sms(), stream) : launch_sus(A, device_sms(), stream);
     if (own) {
         cudaError_t e2 = cudaFreeAsync(ws, stream);

@@ -39,6 +39,8 @@ struct CodeDev {
     const int* cedge;    // [E] edge ids of each column, rows increasing
     const uint8_t* gexp; // [512] x^i, extended so that i < 2(q-1) needs no reduction
     const uint8_t* glog; // [256] log_x(a) for a != 0
+    const int4* cinfo;   // [E] per column slot: {edge, row start, row degree | h << 8, row}
+    const uint8_t* cdep; // [N] 1 when column j shares a check with column j-1
 };
 
 struct DecodeArgs {
@@ -217,37 +219,204 @@ __device__ __forceinline__ int gf_div(const uint8_t* ex, const uint8_t* lg, int 
     return b ? ex[lg[b] + (Q - 1) - lg[h]] : 0;
 }
 
-// Horizontal-pass epilogue (Eq. 3 through the XOR-convolution theorem):
-// G is the product of the other edges' transforms; s = WHT(G)/q is the
-// distribution of y = sum h_m x_m over the other edges; r[a] = s[z + h a]
-// (GF addition = XOR), negatives from rounding set to 0, normalised.
-template <int Q>
-__device__ __forceinline__ void check_finish(float (&x)[Lay<Q>::V], int h, int z, float* sc, unsigned mask, int g,
-                                             const uint8_t* ex, const uint8_t* lg) {
-    constexpr int V = Lay<Q>::V;
-    wht<Q>(x, mask, g);
-#pragma unroll
-    for (int i = 0; i < V; i++) sc[g * V + i] = fmaxf(x[i] * (1.0f / Q), 0.0f);
-    __syncwarp(mask);
-#pragma unroll
-    for (int i = 0; i < V; i++) x[i] = sc[z ^ gf_mul(ex, lg, h, g * V + i)];
-    __syncwarp(mask);
-    gnormalise<Q>(x, mask);
+// ------------------------------------------------------------------------
+// Transform-domain representation of a message (the XOR-convolution theorem
+// behind Eq. 3, kept accurate in FP32).
+//
+// For a message q_ij let y = h_ij x_j (the relabelled symbol, distribution
+// qt[y] = q[h^-1 y]) and c its most likely value.  The stored vector is
+//     D[w] = 1 - WHT(u)[w] = 2 * sum_{b : parity(b & w) = 1} u[b],
+// with u[b] = qt[b XOR c] the distribution shifted so that its mode sits at
+// 0.  D[0] is always 0, so slot 0 carries c instead.  D is formed with
+// additions of non-negative numbers only, so peaked messages (WHT entries
+// within 1e-7 of 1, which plain FP32 transforms round away) keep their
+// small deviations to relative precision.
+//
+// The horizontal pass multiplies transforms, prod_m (1 - D_m) = 1 - E with
+// E <- E + D (1 - E), XORs the shifts C = XOR_m c_m, and inverts:
+//     s[a] = [a = 0] - WHT(E)[a] / q
+// is the distribution of sum_m h_m x_m XOR C, so r_ij[a] = s[z XOR C XOR h a].
+// ------------------------------------------------------------------------
+
+// Load a stored vector; lane 0 of the group takes the shift out of slot 0.
+template <int V>
+__device__ __forceinline__ void ld_dev(float (&D)[V], int& c, const float* p, int g) {
+    ldv<V>(D, p);
+    c = 0;
+    if (g == 0) {
+        c = (int)D[0];
+        D[0] = 0.f;
+    }
 }
 
-// Vertical-pass epilogue: the distribution of h x for x ~ q (entry b = h a
-// takes q[a]) and its transform, ready for the next horizontal pass.
-template <int Q>
-__device__ __forceinline__ void to_transform(float (&x)[Lay<Q>::V], int h, float* sc, unsigned mask, int g,
+template <int V>
+__device__ __forceinline__ void dev_combine(float (&E)[V], const float (&D)[V]) {
+#pragma unroll
+    for (int v = 0; v < V; v++) E[v] = fmaf(D[v], 1.0f - E[v], E[v]);
+}
+
+template <int Q, int NB>
+__device__ __forceinline__ void wht_n(float (&x)[NB][Lay<Q>::V], unsigned mask, int g) {
+    constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+#pragma unroll
+    for (int h = 1; h < V; h <<= 1) {
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+#pragma unroll
+            for (int i = 0; i < V; i++) {
+                if (!(i & h)) {
+                    const float a = x[k][i], b = x[k][i + h];
+                    x[k][i] = a + b;
+                    x[k][i + h] = a - b;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 1; m < G; m <<= 1) {
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+#pragma unroll
+            for (int i = 0; i < V; i++) {
+                const float o = __shfl_xor_sync(mask, x[k][i], m);
+                x[k][i] = (g & m) ? (o - x[k][i]) : (x[k][i] + o);
+            }
+        }
+    }
+}
+
+// Horizontal-pass epilogue for NB vectors at once (n of them in use): from
+// E (and the XOR of shifts C, the same in every lane) to r_ij, normalised;
+// negatives from rounding are set to 0.  sc holds NB*Q floats.
+template <int Q, int NB>
+__device__ __forceinline__ void dev_finish_n(float (&x)[NB][Lay<Q>::V], const int (&C)[NB], const int (&h)[NB],
+                                             const int (&z)[NB], int n, float* sc, unsigned mask, int g,
                                              const uint8_t* ex, const uint8_t* lg) {
     constexpr int V = Lay<Q>::V;
+    wht_n<Q, NB>(x, mask, g);
 #pragma unroll
-    for (int i = 0; i < V; i++) sc[g * V + i] = x[i];
+    for (int k = 0; k < NB; k++) {
+        if (k < n) {
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const int a = g * V + v;
+                const float t = x[k][v] * (1.0f / Q);
+                sc[k * Q + a] = fmaxf(a == 0 ? 1.0f - t : -t, 0.0f);
+            }
+        }
+    }
     __syncwarp(mask);
 #pragma unroll
-    for (int i = 0; i < V; i++) x[i] = sc[gf_div<Q>(ex, lg, g * V + i, h)];
+    for (int k = 0; k < NB; k++) {
+        if (k < n) {
+#pragma unroll
+            for (int v = 0; v < V; v++) x[k][v] = sc[k * Q + ((z[k] ^ C[k] ^ gf_mul(ex, lg, h[k], g * V + v)) & (Q - 1))];
+        }
+    }
     __syncwarp(mask);
-    wht<Q>(x, mask, g);
+#pragma unroll
+    for (int k = 0; k < NB; k++)
+        if (k < n) gnormalise<Q>(x[k], mask);
+}
+
+// Vertical-pass epilogue for NB normalised messages q (n in use): the stored
+// form D (slot 0 = shift) of the distribution of h x.  Two-channel
+// butterflies carry the even- and odd-parity masses, additions only.
+template <int Q, int NB>
+__device__ __forceinline__ void to_deviation_n(float (&x)[NB][Lay<Q>::V], const int (&h)[NB], int n, float* sc,
+                                               unsigned mask, int g, const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+    int c[NB];
+#pragma unroll
+    for (int k = 0; k < NB; k++) {
+        c[k] = 0;
+        if (k < n) {
+            const int am = gargmax<Q>(x[k], mask, g);
+            c[k] = gf_mul(ex, lg, h[k], am);
+#pragma unroll
+            for (int v = 0; v < V; v++) sc[k * Q + g * V + v] = x[k][v];
+        }
+    }
+    __syncwarp(mask);
+    float ev[NB][V], od[NB][V];
+#pragma unroll
+    for (int k = 0; k < NB; k++) {
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const int b = g * V + v;
+            ev[k][v] = (k < n && b != 0) ? sc[k * Q + gf_div<Q>(ex, lg, b ^ c[k], h[k])] : 0.0f;
+            od[k][v] = 0.0f;
+        }
+    }
+    __syncwarp(mask);
+#pragma unroll
+    for (int hb = 1; hb < V; hb <<= 1) {
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+#pragma unroll
+            for (int i = 0; i < V; i++) {
+                if (!(i & hb)) {
+                    const int j = i + hb;
+                    const float e0 = ev[k][i], o0 = od[k][i], e1 = ev[k][j], o1 = od[k][j];
+                    ev[k][i] = e0 + e1;
+                    od[k][i] = o0 + o1;
+                    ev[k][j] = e0 + o1;
+                    od[k][j] = o0 + e1;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 1; m < G; m <<= 1) {
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+#pragma unroll
+            for (int i = 0; i < V; i++) {
+                const float pe = __shfl_xor_sync(mask, ev[k][i], m);
+                const float po = __shfl_xor_sync(mask, od[k][i], m);
+                if (g & m) {
+                    const float ne = pe + od[k][i], no = po + ev[k][i];
+                    ev[k][i] = ne;
+                    od[k][i] = no;
+                } else {
+                    ev[k][i] += pe;
+                    od[k][i] += po;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NB; k++) {
+#pragma unroll
+        for (int v = 0; v < V; v++) x[k][v] = 2.0f * od[k][v];
+        if (g == 0) x[k][0] = (float)c[k];
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void to_deviation(float (&x)[Lay<Q>::V], int h, float* sc, unsigned mask, int g,
+                                             const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+    float xx[1][V];
+    const int hh[1] = {h};
+#pragma unroll
+    for (int v = 0; v < V; v++) xx[0][v] = x[v];
+    to_deviation_n<Q, 1>(xx, hh, 1, sc, mask, g, ex, lg);
+#pragma unroll
+    for (int v = 0; v < V; v++) x[v] = xx[0][v];
+}
+
+template <int Q>
+__device__ __forceinline__ void dev_finish(float (&x)[Lay<Q>::V], int C, int h, int z, float* sc, unsigned mask,
+                                           int g, const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+    float xx[1][V];
+    const int cc[1] = {C}, hh[1] = {h}, zz[1] = {z};
+#pragma unroll
+    for (int v = 0; v < V; v++) xx[0][v] = x[v];
+    dev_finish_n<Q, 1>(xx, cc, hh, zz, 1, sc, mask, g, ex, lg);
+#pragma unroll
+    for (int v = 0; v < V; v++) x[v] = xx[0][v];
 }
 
 // p_j: normalised channel likelihood times the block prior of a source symbol.
@@ -300,6 +469,7 @@ __device__ __forceinline__ void markov_prior(const DecodeArgs& A, int f, int i, 
 
 // Launchers (one instantiation set per schedule, see pus.cu / sus.cu).
 cudaError_t launch_channel(const DecodeArgs& A, cudaStream_t s);
+cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s);
 

@@ -18,44 +18,51 @@ namespace {
 
 constexpr int kPusThreads = 256;
 
-// r_ij for every edge of check i: prefix/suffix products of the other edges'
-// transforms (no division: transforms of probability vectors can be 0).
+// r_ij for every edge of check i: prefix/suffix combinations of the other
+// edges' stored vectors (no division: transforms can be exactly 0).
 template <int Q, int DC>
 __device__ __forceinline__ void pus_check(const DecodeArgs& A, float* slab, int f, int i, float* sc, unsigned mask,
                                           int g, const uint8_t* ex, const uint8_t* lg) {
-    constexpr int V = Lay<Q>::V;
+    constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
     const int e0 = A.c.rowptr[i];
     const int d = A.c.rowptr[i + 1] - e0;
     const int z = A.syn ? (A.syn[(size_t)f * A.c.M + i] & (Q - 1)) : 0;
+    const int lane0 = (threadIdx.x & 31) & ~(G - 1);
     float S[DC][V];
+    int Cs[DC];
     float acc[V];
+    int cacc = 0;
 #pragma unroll
-    for (int v = 0; v < V; v++) acc[v] = 1.f;
+    for (int v = 0; v < V; v++) acc[v] = 0.f;
 #pragma unroll
     for (int k = DC - 1; k >= 0; k--) {
         if (k < d) {
 #pragma unroll
             for (int v = 0; v < V; v++) S[k][v] = acc[v];
-            float Fk[V];
-            ldv<V>(Fk, slab + (size_t)(e0 + k) * Q + g * V);
-#pragma unroll
-            for (int v = 0; v < V; v++) acc[v] *= Fk[v];
+            Cs[k] = cacc;
+            float D[V];
+            int c;
+            ld_dev<V>(D, c, slab + (size_t)(e0 + k) * Q + g * V, g);
+            dev_combine<V>(acc, D);
+            cacc ^= c;
         }
     }
     float pre[V];
+    int cpre = 0;
 #pragma unroll
-    for (int v = 0; v < V; v++) pre[v] = 1.f;
+    for (int v = 0; v < V; v++) pre[v] = 0.f;
 #pragma unroll
     for (int k = 0; k < DC; k++) {
         if (k < d) {
-            float Fk[V], x[V];
-            ldv<V>(Fk, slab + (size_t)(e0 + k) * Q + g * V);
+            float D[V], x[V];
+            int c;
+            ld_dev<V>(D, c, slab + (size_t)(e0 + k) * Q + g * V, g);
 #pragma unroll
-            for (int v = 0; v < V; v++) {
-                x[v] = pre[v] * S[k][v];
-                pre[v] *= Fk[v];
-            }
-            check_finish<Q>(x, A.c.eh[e0 + k], z, sc, mask, g, ex, lg);
+            for (int v = 0; v < V; v++) x[v] = fmaf(pre[v], 1.0f - S[k][v], S[k][v]);
+            const int C = __shfl_sync(mask, cpre ^ Cs[k], lane0);
+            dev_combine<V>(pre, D);
+            cpre ^= c;
+            dev_finish<Q>(x, C, A.c.eh[e0 + k], z, sc, mask, g, ex, lg);
             stv<V>(slab + (size_t)(e0 + k) * Q + g * V, x);
         }
     }
@@ -115,7 +122,7 @@ __device__ __forceinline__ void pus_var(const DecodeArgs& A, float* slab, int f,
             }
             gnormalise<Q>(x, mask);
             if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + e) * Q + g * V, x);
-            to_transform<Q>(x, A.c.eh[e], sc, mask, g, ex, lg);
+            to_deviation<Q>(x, A.c.eh[e], sc, mask, g, ex, lg);
             stv<V>(slab + (size_t)e * Q + g * V, x);
         }
     }
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(kPusThreads) k_pus(const DecodeArgs A) {
             } else {
                 prior_vec<Q>(A, f, A.c.ecol[e], x, mask, g);
             }
-            to_transform<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+            to_deviation<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
             stv<V>(slab + (size_t)e * Q + g * V, x);
         }
         __syncthreads();

@@ -1,16 +1,18 @@
 // Sequential updating scheme (SUS; Sec. 2, steps 1-4): one lane group per
 // frame, persistent over a frame counter.  For j = 0..N-1 strictly in order:
 // step 1, r_ij for every check i of column j from the current q of the
-// check's other edges (Eq. 3); step 2, q_ij for column j (Eq. 4); Q_j (Eq. 5)
-// from the same r_ij.  After the sweep: hard decision test H x = z and the
+// check's other edges (Eq. 3); step 2, q_ij for column j (Eq. 4), and Q_j
+// (Eq. 5) from the same r_ij.  After the sweep: the test H x = z and the
 // block-prior update (Eqs. 6-7).  Parallelism inside a frame comes only from
-// the q entries of a vector (the group's lanes); frames run side by side.
+// a column's d_v checks (processed together) and the q entries of a vector
+// (the group's lanes); frames run side by side.
 //
-// The slab holds, per edge, the Walsh-Hadamard transform of the distribution
-// of h_ij x_j under q_ij, so step 1 is a product of stored transforms followed
-// by one inverse transform.  Each lane only ever touches its own slice of
-// every vector in global memory, so no cross-lane memory ordering is needed
-// for the slab.
+// Latency: a frame's sweep is a chain of N dependent column steps, so the
+// loads of column j+1 are issued before column j is computed.  They are only
+// stale if column j+1 shares a check with column j (a per-column flag built
+// with the code); then they are issued again after column j's stores.  Each
+// lane only touches its own slice of every stored vector, so program order
+// makes its own stores visible to its later loads.
 #include "gfbp_internal.cuh"
 
 namespace gfbp {
@@ -20,134 +22,207 @@ namespace {
 constexpr int kSusThreads = 128;
 
 template <int Q, int DC, int DV>
+struct ColBuf {
+    float D[DV][DC][Lay<Q>::V];
+    int4 info[DV];
+    int d;
+};
+
+template <int Q, int DC, int DV>
+__device__ __forceinline__ void load_col(ColBuf<Q, DC, DV>& b, const DecodeArgs& A, const float* slab, int j, int g) {
+    constexpr int V = Lay<Q>::V;
+    const int c0 = A.c.colptr[j];
+    b.d = A.c.colptr[j + 1] - c0;
+#pragma unroll
+    for (int k = 0; k < DV; k++)
+        if (k < b.d) b.info[k] = A.c.cinfo[c0 + k];
+#pragma unroll
+    for (int k = 0; k < DV; k++) {
+        if (k < b.d) {
+            const int e0 = b.info[k].y, dc = b.info[k].z & 255;
+#pragma unroll
+            for (int m = 0; m < DC; m++)
+                if (m < dc) ldv<V>(b.D[k][m], slab + (size_t)(e0 + m) * Q + g * V);
+        }
+    }
+}
+
+// Steps 1-2 for column j once E (the combined other-edge vectors) and C (the
+// XOR of their shifts) are known for each of the column's d checks.
+template <int Q, int DV>
+__device__ __forceinline__ void sus_column_tail(const DecodeArgs& A, float* slab, int f, int j, int d,
+                                                float (&E)[DV][Lay<Q>::V], const int (&C)[DV], const int (&eid)[DV],
+                                                const int (&h)[DV], const int (&z)[DV], uint8_t* xh, float* sc,
+                                                unsigned mask, int g, const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+    const int N = A.c.N;
+    dev_finish_n<Q, DV>(E, C, h, z, d, sc, mask, g, ex, lg);  // E now holds r_ij
+    float p[V];
+    prior_vec<Q>(A, f, j, p, mask, g);
+    float S[DV][V], acc[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = 1.f;
+#pragma unroll
+    for (int k = DV - 1; k >= 0; k--) {
+        if (k < d) {
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                S[k][v] = acc[v];
+                acc[v] *= E[k][v];
+            }
+        }
+    }
+    {
+        float Qj[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) Qj[v] = p[v] * acc[v];
+        gnormalise<Q>(Qj, mask);
+        const int a = gargmax<Q>(Qj, mask, g);
+        if (g == 0) xh[j] = (uint8_t)a;
+        if (A.post) stv<V>(A.post + ((size_t)f * N + j) * Q + g * V, Qj);
+        if (A.markov) {
+            const int si = A.src_index[j];
+            if (si >= 0) stv<V>(A.Qsrc + ((size_t)f * A.K + si) * Q + g * V, Qj);
+        }
+    }
+    float pre[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) pre[v] = 1.f;
+#pragma unroll
+    for (int k = 0; k < DV; k++) {
+        if (k < d) {
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const float r = E[k][v];
+                E[k][v] = p[v] * (pre[v] * S[k][v]);
+                pre[v] *= r;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < DV; k++) {
+        if (k < d) {
+            gnormalise<Q>(E[k], mask);
+            if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + eid[k]) * Q + g * V, E[k]);
+        }
+    }
+    to_deviation_n<Q, DV>(E, h, d, sc, mask, g, ex, lg);
+#pragma unroll
+    for (int k = 0; k < DV; k++)
+        if (k < d) stv<V>(slab + (size_t)eid[k] * Q + g * V, E[k]);
+}
+
+template <int Q, int DC, int DV>
 __global__ void __launch_bounds__(kSusThreads) k_sus(const DecodeArgs A) {
     constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+    // keep both column buffers in registers only while they are small
+    constexpr bool PF = (2 * DV * DC * V <= 160);
     __shared__ uint8_t s_exp[512];
     __shared__ uint8_t s_log[256];
-    __shared__ __align__(16) float s_scr[kSusThreads * V];
+    __shared__ __align__(16) float s_scr[kSusThreads * V * DV];
 
     const int tid = threadIdx.x;
     const int g = tid & (G - 1);
     const int grp = tid / G;
     const unsigned mask = group_mask<G>();
-    float* sc = s_scr + grp * Q;
+    const int lane0 = (threadIdx.x & 31) & ~(G - 1);
+    float* sc = s_scr + grp * Q * DV;
     for (int k = tid; k < 512; k += blockDim.x) s_exp[k] = A.c.gexp[k];
     for (int k = tid; k < 256; k += blockDim.x) s_log[k] = A.c.glog[k];
     __syncthreads();
     const int M = A.c.M, N = A.c.N;
     const long long E = A.c.E;
-    const int* __restrict__ rowptr = A.c.rowptr;
-    const int* __restrict__ colptr = A.c.colptr;
-    const int* __restrict__ cedge = A.c.cedge;
-    const int* __restrict__ erow = A.c.erow;
-    const uint8_t* __restrict__ eh = A.c.eh;
 
     for (;;) {
         int f = 0;
         if (g == 0) f = atomicAdd(A.work, 1);
-        f = __shfl_sync(mask, f, threadIdx.x & 31 & ~(G - 1));
+        f = __shfl_sync(mask, f, lane0);
         if (f >= A.F) break;
         float* slab = A.msg + (size_t)f * E * Q;
         const uint8_t* zf = A.syn ? A.syn + (size_t)f * M : nullptr;
         uint8_t* xh = A.xhat + (size_t)f * N;
 
-        for (long long e = 0; e < E; e++) {
-            float x[V];
-            if (A.step) {
-                ldv<V>(x, A.msg_io + ((size_t)f * E + e) * Q + g * V);
-            } else {
-                prior_vec<Q>(A, f, A.c.ecol[e], x, mask, g);
-            }
-            to_transform<Q>(x, eh[e], sc, mask, g, s_exp, s_log);
-            stv<V>(slab + (size_t)e * Q + g * V, x);
-        }
-
         int t = 1, ok = 0;
         for (;; t++) {
-            for (int j = 0; j < N; j++) {
-                const int c0 = colptr[j];
-                const int d = colptr[j + 1] - c0;
-                // step 1: r_ij for every check i of column j
-                float R[DV][V];
+            if constexpr (PF) {
+                ColBuf<Q, DC, DV> cur, nxt;
+                load_col<Q, DC, DV>(cur, A, slab, 0, g);
+                for (int j = 0; j < N; j++) {
+                    if (j + 1 < N) load_col<Q, DC, DV>(nxt, A, slab, j + 1, g);
+                    const int d = cur.d;
+                    float Ek[DV][V];
+                    int C[DV], eid[DV], h[DV], z[DV];
 #pragma unroll
-                for (int k = 0; k < DV; k++) {
-                    if (k < d) {
-                        const int e = cedge[c0 + k];
-                        const int i = erow[e];
-                        const int e0 = rowptr[i];
-                        const int dc = rowptr[i + 1] - e0;
-                        float x[V];
+                    for (int k = 0; k < DV; k++) {
+                        C[k] = 0;
 #pragma unroll
-                        for (int v = 0; v < V; v++) x[v] = 1.f;
+                        for (int v = 0; v < V; v++) Ek[k][v] = 0.f;
+                        if (k < d) {
+                            const int4 in = cur.info[k];
+                            eid[k] = in.x;
+                            h[k] = (in.z >> 8) & 255;
+                            z[k] = zf ? (zf[in.w] & (Q - 1)) : 0;
+                            const int own = in.x - in.y, dc = in.z & 255;
 #pragma unroll
-                        for (int m = 0; m < DC; m++) {
-                            if (m < dc && e0 + m != e) {
-                                float y[V];
-                                ldv<V>(y, slab + (size_t)(e0 + m) * Q + g * V);
+                            for (int m = 0; m < DC; m++) {
+                                if (m < dc && m != own) {
+                                    if (g == 0) {
+                                        C[k] ^= (int)cur.D[k][m][0];
+                                        cur.D[k][m][0] = 0.f;
+                                    }
+                                    dev_combine<V>(Ek[k], cur.D[k][m]);
+                                }
+                            }
+                        } else {
+                            eid[k] = 0; h[k] = 1; z[k] = 0;
+                        }
+                        C[k] = __shfl_sync(mask, C[k], lane0);
+                    }
+                    sus_column_tail<Q, DV>(A, slab, f, j, d, Ek, C, eid, h, z, xh, sc, mask, g, s_exp, s_log);
+                    if (j + 1 < N) {
+                        if (A.c.cdep[j + 1]) load_col<Q, DC, DV>(nxt, A, slab, j + 1, g);
+                        cur = nxt;
+                    }
+                }
+            } else {
+                for (int j = 0; j < N; j++) {
+                    const int c0 = A.c.colptr[j];
+                    const int d = A.c.colptr[j + 1] - c0;
+                    float Ek[DV][V];
+                    int C[DV], eid[DV], h[DV], z[DV];
 #pragma unroll
-                                for (int v = 0; v < V; v++) x[v] *= y[v];
+                    for (int k = 0; k < DV; k++) {
+                        C[k] = 0;
+#pragma unroll
+                        for (int v = 0; v < V; v++) Ek[k][v] = 0.f;
+                        eid[k] = 0; h[k] = 1; z[k] = 0;
+                        if (k < d) {
+                            const int4 in = A.c.cinfo[c0 + k];
+                            eid[k] = in.x;
+                            h[k] = (in.z >> 8) & 255;
+                            z[k] = zf ? (zf[in.w] & (Q - 1)) : 0;
+                            const int e0 = in.y, dc = in.z & 255;
+                            for (int m = 0; m < dc; m++) {
+                                if (e0 + m == in.x) continue;
+                                float D[V];
+                                int c;
+                                ld_dev<V>(D, c, slab + (size_t)(e0 + m) * Q + g * V, g);
+                                C[k] ^= c;
+                                dev_combine<V>(Ek[k], D);
                             }
                         }
-                        check_finish<Q>(x, eh[e], zf ? (zf[i] & (Q - 1)) : 0, sc, mask, g, s_exp, s_log);
-#pragma unroll
-                        for (int v = 0; v < V; v++) R[k][v] = x[v];
+                        C[k] = __shfl_sync(mask, C[k], lane0);
                     }
-                }
-                // step 2: q_ij for column j, and Q_j
-                float p[V];
-                prior_vec<Q>(A, f, j, p, mask, g);
-                float S[DV][V], acc[V];
-#pragma unroll
-                for (int v = 0; v < V; v++) acc[v] = 1.f;
-#pragma unroll
-                for (int k = DV - 1; k >= 0; k--) {
-                    if (k < d) {
-#pragma unroll
-                        for (int v = 0; v < V; v++) {
-                            S[k][v] = acc[v];
-                            acc[v] *= R[k][v];
-                        }
-                    }
-                }
-                {
-                    float Qj[V];
-#pragma unroll
-                    for (int v = 0; v < V; v++) Qj[v] = p[v] * acc[v];
-                    gnormalise<Q>(Qj, mask);
-                    const int a = gargmax<Q>(Qj, mask, g);
-                    if (g == 0) xh[j] = (uint8_t)a;
-                    if (A.post) stv<V>(A.post + ((size_t)f * N + j) * Q + g * V, Qj);
-                    if (A.markov) {
-                        const int si = A.src_index[j];
-                        if (si >= 0) stv<V>(A.Qsrc + ((size_t)f * A.K + si) * Q + g * V, Qj);
-                    }
-                }
-                float pre[V];
-#pragma unroll
-                for (int v = 0; v < V; v++) pre[v] = 1.f;
-#pragma unroll
-                for (int k = 0; k < DV; k++) {
-                    if (k < d) {
-                        const int e = cedge[c0 + k];
-                        float x[V];
-#pragma unroll
-                        for (int v = 0; v < V; v++) {
-                            x[v] = p[v] * (pre[v] * S[k][v]);
-                            pre[v] *= R[k][v];
-                        }
-                        gnormalise<Q>(x, mask);
-                        if (A.step) stv<V>(A.msg_io + ((size_t)f * E + e) * Q + g * V, x);
-                        to_transform<Q>(x, eh[e], sc, mask, g, s_exp, s_log);
-                        stv<V>(slab + (size_t)e * Q + g * V, x);
-                    }
+                    sus_column_tail<Q, DV>(A, slab, f, j, d, Ek, C, eid, h, z, xh, sc, mask, g, s_exp, s_log);
                 }
             }
             __syncwarp(mask);
-            // hard decisions are in xh; test H x = z over the group's lanes
+            // the hard decisions of the sweep are in xh: test H x = z
             int bad = 0;
             for (int i = g; i < M; i += G) {
                 int s = 0;
-                for (int e = rowptr[i]; e < rowptr[i + 1]; e++) s ^= gf_mul(s_exp, s_log, eh[e], xh[A.c.ecol[e]]);
+                for (int e = A.c.rowptr[i]; e < A.c.rowptr[i + 1]; e++)
+                    s ^= gf_mul(s_exp, s_log, A.c.eh[e], xh[A.c.ecol[e]]);
                 bad |= (s != (zf ? (zf[i] & (Q - 1)) : 0));
             }
 #pragma unroll
@@ -178,6 +253,35 @@ __global__ void __launch_bounds__(kSusThreads) k_sus(const DecodeArgs A) {
     }
 }
 
+// q_ij <- p_j (Sec. 2 initialisation) or the caller's state, in stored form,
+// one lane group per (frame, edge).
+template <int Q>
+__global__ void __launch_bounds__(256) k_init_dev(const DecodeArgs A) {
+    constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+    __shared__ uint8_t s_exp[512];
+    __shared__ uint8_t s_log[256];
+    __shared__ __align__(16) float s_scr[256 * V];
+    for (int k = threadIdx.x; k < 512; k += blockDim.x) s_exp[k] = A.c.gexp[k];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_log[k] = A.c.glog[k];
+    __syncthreads();
+    const int g = threadIdx.x & (G - 1);
+    const int grp = threadIdx.x / G;
+    const unsigned mask = group_mask<G>();
+    float* sc = s_scr + grp * Q;
+    const long long E = A.c.E;
+    const long long total = (long long)A.F * E;
+    const long long stride = (long long)gridDim.x * (blockDim.x / G);
+    for (long long it = (long long)blockIdx.x * (blockDim.x / G) + grp; it < total; it += stride) {
+        const int f = (int)(it / E);
+        const long long e = it % E;
+        float x[V];
+        if (A.step) ldv<V>(x, A.msg_io + (size_t)it * Q + g * V);
+        else prior_vec<Q>(A, f, A.c.ecol[e], x, mask, g);
+        to_deviation<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+        stv<V>(A.msg + (size_t)it * Q + g * V, x);
+    }
+}
+
 template <int Q, int DC, int DV>
 cudaError_t launch_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr int G = Lay<Q>::G;
@@ -202,6 +306,17 @@ cudaError_t launch_deg(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     return launch_q<Q, 16, 8>(A, num_sms, s);
 }
 
+template <int Q>
+cudaError_t launch_init_q(const DecodeArgs& A, cudaStream_t s) {
+    constexpr int G = Lay<Q>::G;
+    const long long total = (long long)A.F * A.c.E;
+    long long blocks = (total + (256 / G) - 1) / (256 / G);
+    if (blocks > 65535LL * 16) blocks = 65535LL * 16;
+    if (blocks < 1) return cudaSuccess;
+    k_init_dev<Q><<<(unsigned)blocks, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
@@ -214,6 +329,20 @@ cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     case 64: return launch_deg<64>(A, num_sms, s);
     case 128: return launch_deg<128>(A, num_sms, s);
     case 256: return launch_deg<256>(A, num_sms, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s) {
+    switch (A.c.q) {
+    case 2: return launch_init_q<2>(A, s);
+    case 4: return launch_init_q<4>(A, s);
+    case 8: return launch_init_q<8>(A, s);
+    case 16: return launch_init_q<16>(A, s);
+    case 32: return launch_init_q<32>(A, s);
+    case 64: return launch_init_q<64>(A, s);
+    case 128: return launch_init_q<128>(A, s);
+    case 256: return launch_init_q<256>(A, s);
     }
     return cudaErrorInvalidValue;
 }
