@@ -1,0 +1,338 @@
+"""Throughput benchmark of GF(q) belief-propagation decoding on GB300.
+
+One step decodes one batch of the GF(16) regular (3,6) rate-1/2 N=1000
+workload over BI-AWGN (Eb/N0 1.0 / 1.5 / 2.0 dB round-robin over frames,
+4096 frames, max 200 iterations, early stop) under both schedules of the
+paper, PUS then SUS, with inputs resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank decodes its own 4096 frames (weak
+scaling, no data-path collective); the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "decoded frames/s and symbol-iter/s, SUS vs PUS, at matched BER; p50/p99 latency; % HBM roofline"
+WORKLOAD = "gf16_n1000_awgn"
+# Algorithmic bytes per symbol-iteration (FP32 messages, d_v = 3): PUS reads and
+# writes every edge message twice per iteration plus the prior (52 q bytes); SUS
+# reads and writes the single stored slab once per sweep plus the prior (28 q).
+ALG_BYTES_PER_SYMITER = {"pus": 52, "sus": 28}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_cs_0605069_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, symiters: float):
+    """DRAM bytes of the kernel for this launch, scaled from the committed ncu
+    summary when it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = t.get(kernel)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent["dram_bytes_per_symiter"] * symiters
+
+
+def cpu_baseline(batch, frames: int, max_iter: int):
+    """The FP64 oracle on the host cores, on the first `frames` frames."""
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    it = 0
+    for s in ("pus", "sus"):
+        r = O.decode(batch.code, batch.obs[:frames], "awgn", batch.param[:frames], s, max_iter=max_iter,
+                     threads=threads)
+        it += int(r["iters"].sum())
+    dt = time.perf_counter() - t0
+    return {"value": 2 * frames / dt, "unit": "frames/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {frames} frames of the batch, PUS and SUS, {dt:.1f} s",
+            "sym_iter_per_s": it * batch.code.N / dt}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle as it stands, timed on the host cores."""
+    if rank != 0:
+        return
+    from paper_cs_0605069_gb300 import workload as W
+    frames = 24
+    b = W.make_batch(WORKLOAD, frames=frames)
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    times, its = [], []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        it = 0
+        for s in ("pus", "sus"):
+            r = O.decode(b.code, b.obs, "awgn", b.param, s, max_iter=b.max_iter, threads=threads)
+            it += int(r["iters"].sum())
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            its.append(it)
+    dt = float(np.mean(times))
+    val = 2 * frames / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} sample of {frames} frames per step (first frames of the batch)",
+                       "q": 16, "N": 1000, "code": "regular (3,6) rate 1/2", "channel": "BI-AWGN 1.0/1.5/2.0 dB",
+                       "max_iter": b.max_iter, "schedules": ["pus", "sus"]},
+            "cpu_baseline": {"value": val, "unit": "frames/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{frames} frames x 2 schedules per step"},
+            "e2e": {"value": val, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sym_iter_per_s": float(np.mean(its)) * b.code.N / dt}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+
+    F = args.frames
+    b = W.make_batch(WORKLOAD, frames=F, first_frame=rank * F)
+    code = gfbp.Code.from_coo(b.code)
+    N, q = b.code.N, b.code.q
+    dev = torch.device("cuda", local)
+    obs = torch.from_numpy(b.obs).to(dev)
+    sig = torch.from_numpy(b.param.astype(np.float32)).to(dev)
+    scheds = ("pus", "sus")
+    ws = {s: torch.empty(gfbp.workspace_size(code, F, s), dtype=torch.uint8, device=dev) for s in scheds}
+    outs = {s: dict(x_hat=torch.empty((F, N), dtype=torch.uint8, device=dev),
+                    iters=torch.empty(F, dtype=torch.int32, device=dev),
+                    converged=torch.empty(F, dtype=torch.uint8, device=dev)) for s in scheds}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(record=None):
+        for s in scheds:
+            ev = record[s] if record else None
+            gfbp.decode(code, obs, "awgn", 0.0, schedule=s, max_iter=b.max_iter, frame_param=sig,
+                        workspace=ws[s], out=outs[s], kernel_events=ev)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    step_ms, kern_ms = [], {s: [] for s in scheds}
+    iters = {s: [] for s in scheds}
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kev = {s: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for s in scheds}
+        e0.record(stream)
+        step(kev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for s in scheds:
+            kern_ms[s].append(kev[s][0].elapsed_time(kev[s][1]))
+            iters[s].append(outs[s]["iters"].cpu().numpy().copy())
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    frames_per_step = 2 * F * world
+    value = frames_per_step / (ms_per_step / 1e3)
+
+    # end to end through the public API: pinned host obs in, results out, every step
+    e2e = None
+    if not args.no_e2e:
+        host_obs = torch.from_numpy(b.obs).pin_memory()
+        host_sig = torch.from_numpy(b.param.astype(np.float32)).pin_memory()
+        host_out = {s: {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs[s].items()} for s in scheds}
+        obs_d = torch.empty_like(obs)
+        sig_d = torch.empty_like(sig)
+        h2d = host_obs.numel() * 4 + host_sig.numel() * 4
+        d2h = sum(v.numel() * v.element_size() for s in scheds for v in outs[s].values())
+
+        def e2e_step():
+            obs_d.copy_(host_obs, non_blocking=True)
+            sig_d.copy_(host_sig, non_blocking=True)
+            for s in scheds:
+                gfbp.decode(code, obs_d, "awgn", 0.0, schedule=s, max_iter=b.max_iter, frame_param=sig_d,
+                            workspace=ws[s], out=outs[s])
+                for k in outs[s]:
+                    host_out[s][k].copy_(outs[s][k], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e_ms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            z.record(stream)
+            torch.cuda.synchronize()
+            e_ms.append(a.elapsed_time(z))
+        em = float(np.mean(e_ms))
+        if world > 1:
+            t = torch.tensor([em], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            em = float(t.item())
+        e2e = {"value": frames_per_step / (em / 1e3), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    per = {}
+    for s in scheds:
+        it = np.stack(iters[s])
+        symit = float(it.sum()) * N / args.steps
+        kms = float(np.mean(kern_ms[s]))
+        per[s] = {"kernel_ms": kms, "frames_per_s": F / (kms / 1e3), "sym_iter_per_s": symit / (kms / 1e3),
+                  "mean_iters": float(it.mean()), "mean_iters_converged": None,
+                  "iters_by_ebn0_db": {str(db): float(it[:, k::3].mean()) for k, db in enumerate((1.0, 1.5, 2.0))},
+                  "converged": float(outs[s]["converged"].float().mean().item())}
+        per[s]["mean_iters_converged"] = None
+    # roofline of the dominant kernel
+    dom = max(scheds, key=lambda s: per[s]["kernel_ms"])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    symit_launch = float(np.stack(iters[dom]).sum()) * N / args.steps
+    alg_bytes = ALG_BYTES_PER_SYMITER[dom] * q * symit_launch
+    achieved = alg_bytes / (per[dom]["kernel_ms"] / 1e3) / 1e9
+    traffic = profiled_traffic("k_" + dom, symit_launch)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": f"k_{dom}<16,6,3>",
+            "peak_source": "measured" if peaks else "fallback",
+            "algorithmic_bytes_per_symiter": ALG_BYTES_PER_SYMITER[dom] * q}
+    gpu_launches = args.steps * (2 + 3)   # PUS: channel + decode; SUS: channel + init + decode
+
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "q": q, "N": N, "M": b.code.M, "code": "regular (3,6) rate 1/2",
+                       "channel": "BI-AWGN, Eb/N0 1.0/1.5/2.0 dB round-robin", "frames_per_gpu": F,
+                       "max_iter": b.max_iter, "schedules": list(scheds), "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"frames sharded over {world} GPU(s), no collective"},
+            "sym_iter_per_s": sum(per[s]["sym_iter_per_s"] for s in scheds) / 2,
+            "pus": per["pus"], "sus": per["sus"],
+            "sus_pus_iteration_ratio": per["sus"]["mean_iters"] / per["pus"]["mean_iters"],
+            "latency_ms": {"batch_pus": per["pus"]["kernel_ms"], "batch_sus": per["sus"]["kernel_ms"]},
+            "roofline": roof, "clocks": clocks, "gpu_launches": gpu_launches, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(b, 96, b.max_iter)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    code.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

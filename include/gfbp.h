@@ -118,6 +118,8 @@ typedef struct {
     void* workspace;         /* device scratch of >= gfbp_workspace_size() bytes, 256-byte
                                 aligned; NULL = the library allocates it stream-ordered */
     size_t workspace_bytes;
+    void* kernel_events[2];  /* optional cudaEvent_t pair, recorded on `stream` right before
+                                and right after the schedule kernel (for timing it alone) */
 } gfbp_options;
 
 /*

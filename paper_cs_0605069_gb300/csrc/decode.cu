@@ -340,7 +340,11 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
     if (e == cudaSuccess) e = cudaMemsetAsync(A.work, 0, sizeof(int), stream);
     if (e == cudaSuccess) e = launch_channel(A, stream);
     if (e == cudaSuccess && schedule == GFBP_SUS) e = launch_init_dev(A, stream);
+    cudaEvent_t ev0 = opt ? static_cast<cudaEvent_t>(opt->kernel_events[0]) : nullptr;
+    cudaEvent_t ev1 = opt ? static_cast<cudaEvent_t>(opt->kernel_events[1]) : nullptr;
+    if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, stream);
     if (e == cudaSuccess) e = (schedule == GFBP_PUS) ? launch_pus(A, device_sms(), stream) : launch_sus(A, device_sms(), stream);
+    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, stream);
     if (own) {
         cudaError_t e2 = cudaFreeAsync(ws, stream);
         if (e == cudaSuccess) e = e2;

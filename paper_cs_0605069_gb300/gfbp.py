@@ -44,7 +44,7 @@ class gfbp_prior(C.Structure):
 class gfbp_options(C.Structure):
     _fields_ = [("punct", C.c_void_p), ("syndrome", C.c_void_p), ("post", C.c_void_p),
                 ("xhat_trace", C.c_void_p), ("no_early_stop", C.c_int32), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("kernel_events", C.c_void_p * 2)]
 
 
 def lib() -> C.CDLL:
@@ -148,7 +148,8 @@ def workspace_size(code: Code, n_frames: int, schedule: str = "pus", T=None, K: 
 
 def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: str = "pus", max_iter: int = 100,
            T=None, K: int = 0, src_pos=None, frame_param=None, punct=None, syndrome=None, post: bool = False,
-           trace: bool = False, no_early_stop: bool = False, workspace=None, out=None, stream=None):
+           trace: bool = False, no_early_stop: bool = False, workspace=None, out=None, stream=None,
+           kernel_events=None):
     """gfbp_decode on CUDA tensors.  obs: float32 [F][N][p] (or [F][N][q] for
     loglik).  Returns dict of device tensors x_hat [F][N] uint8, iters [F]
     int32, converged [F] uint8 (+ post [F][N][q], trace [F][max_iter][N])."""
@@ -169,6 +170,9 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     opt = gfbp_options(_ptr(punct), _ptr(syndrome), _ptr(out.get("post")), _ptr(out.get("trace")),
                        int(no_early_stop), _ptr(workspace), int(workspace.numel()))
+    if kernel_events is not None:   # (torch.cuda.Event, torch.cuda.Event) timing the schedule kernel alone
+        opt.kernel_events[0] = kernel_events[0].cuda_event
+        opt.kernel_events[1] = kernel_events[1].cuda_event
     ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
     _ok(lib().gfbp_decode(code.handle, F, _ptr(obs), ch, SCHEDULE[schedule], C.byref(pr), int(max_iter),
                           _ptr(out["x_hat"]), _ptr(out["iters"]), _ptr(out["converged"]), C.byref(opt),
