@@ -107,6 +107,20 @@ typedef struct {
                                NULL = 0..K-1 */
 } gfbp_prior;
 
+/*
+ * Arithmetic of the horizontal pass (Eq. 3).  Both compute the same r_ij:
+ *   TRANSFORM  the XOR-convolution theorem: Walsh-Hadamard transforms of the
+ *              relabelled messages, pointwise product, inverse transform; stored
+ *              as mode-shifted deviations formed with additions only (any q).
+ *              Entries far below the largest keep an absolute error of about
+ *              1e-7 of the largest.
+ *   DIRECT     the configuration sum by successive XOR-convolutions of the
+ *              relabelled messages, non-negative arithmetic only, every entry
+ *              to relative precision (q <= 16).
+ *   AUTO       DIRECT for q <= 16, TRANSFORM above.
+ */
+typedef enum { GFBP_CHECK_AUTO = 0, GFBP_CHECK_TRANSFORM = 1, GFBP_CHECK_DIRECT = 2 } gfbp_check_method;
+
 /* Optional inputs and outputs of gfbp_decode / gfbp_step (NULL = defaults). */
 typedef struct {
     const uint8_t* punct;    /* device [N]: 1 = symbol not observed (uniform likelihood) */
@@ -120,6 +134,7 @@ typedef struct {
     size_t workspace_bytes;
     void* kernel_events[2];  /* optional cudaEvent_t pair, recorded on `stream` right before
                                 and right after the schedule kernel (for timing it alone) */
+    int32_t check_method;    /* gfbp_check_method for the horizontal pass (Eq. 3) */
 } gfbp_options;
 
 /*

@@ -294,6 +294,18 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
     A.step = step;
     A.msg_io = msg_io;
     A.prior_out = prior_out;
+    {
+        const int m = opt ? opt->check_method : GFBP_CHECK_AUTO;
+        if (m == GFBP_CHECK_DIRECT && c.q > 16) {
+            set_error("check_method DIRECT needs q <= 16");
+            return GFBP_EUNSUPPORTED;
+        }
+        if (m < GFBP_CHECK_AUTO || m > GFBP_CHECK_DIRECT) {
+            set_error("unknown check_method");
+            return GFBP_EINVAL;
+        }
+        A.method = (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > 16)) ? kTransform : kDirect;
+    }
 
     void* ws = opt ? opt->workspace : nullptr;
     bool own = false;

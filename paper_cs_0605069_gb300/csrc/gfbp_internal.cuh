@@ -77,6 +77,7 @@ struct DecodeArgs {
     int step;
     float* msg_io;         // [F][E][q] q_ij in (before) and out (after)
     float* prior_out;      // [F][K][q]
+    int method;            // Method
 };
 
 // ---------------------------------------------------------------- helpers
@@ -419,6 +420,93 @@ __device__ __forceinline__ void dev_finish(float (&x)[Lay<Q>::V], int C, int h, 
     for (int v = 0; v < V; v++) x[v] = xx[0][v];
 }
 
+// ------------------------------------------------------------------------
+// Probability-domain route of Eq. 3 (q <= 16): the stored vector of edge ij is
+// qt[y] = q_ij[h^-1 y], the distribution of y = h_ij x_j, and the horizontal
+// pass convolves the other edges' vectors directly,
+//     (a * b)[y] = sum_x a[x] b[x XOR y],
+// which adds non-negative products only, so every entry keeps its relative
+// precision however small it is.
+// ------------------------------------------------------------------------
+
+// Relabel NB normalised messages (n in use) into their stored form qt.
+template <int Q, int NB>
+__device__ __forceinline__ void to_relabelled_n(float (&x)[NB][Lay<Q>::V], const int (&h)[NB], int n, float* sc,
+                                                unsigned mask, int g, const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+#pragma unroll
+    for (int k = 0; k < NB; k++)
+        if (k < n) stv<V>(sc + k * Q + g * V, x[k]);
+    __syncwarp(mask);
+#pragma unroll
+    for (int k = 0; k < NB; k++) {
+        if (k < n) {
+#pragma unroll
+            for (int v = 0; v < V; v++) x[k][v] = sc[k * Q + gf_div<Q>(ex, lg, g * V + v, h[k])];
+        }
+    }
+    __syncwarp(mask);
+}
+
+template <int Q>
+__device__ __forceinline__ void to_relabelled(float (&x)[Lay<Q>::V], int h, float* sc, unsigned mask, int g,
+                                              const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+    float xx[1][V];
+    const int hh[1] = {h};
+#pragma unroll
+    for (int v = 0; v < V; v++) xx[0][v] = x[v];
+    to_relabelled_n<Q, 1>(xx, hh, 1, sc, mask, g, ex, lg);
+#pragma unroll
+    for (int v = 0; v < V; v++) x[v] = xx[0][v];
+}
+
+// out[v] = sum_x sa[x] sb[x XOR y] for this lane's outputs y = g*V + v; sa and
+// sb are whole vectors in shared memory (16-byte aligned).  The XOR of a V-block
+// of x with the lane's V-block of y is again a V-block, so every read is a
+// vector load and the inner index permutation is known at compile time.
+template <int Q>
+__device__ __forceinline__ void xconv_sm(float (&out)[Lay<Q>::V], const float* sa, const float* sb, int g) {
+    constexpr int V = Lay<Q>::V;
+    static_assert(V == 2 || V == 4, "direct route needs V in {2, 4}");
+#pragma unroll
+    for (int v = 0; v < V; v++) out[v] = 0.f;
+#pragma unroll
+    for (int xb = 0; xb < Q; xb += V) {
+        float a[V], b[V];
+        ldv<V>(a, sa + xb);
+        ldv<V>(b, sb + (xb ^ (g * V)));
+#pragma unroll
+        for (int xl = 0; xl < V; xl++) {
+#pragma unroll
+            for (int v = 0; v < V; v++) out[v] = fmaf(a[xl], b[xl ^ v], out[v]);
+        }
+    }
+}
+
+// r[a] = s[z XOR h a] from the distribution s of the other edges' sum, normalised.
+template <int Q, int NB>
+__device__ __forceinline__ void direct_finish_n(float (&x)[NB][Lay<Q>::V], const int (&h)[NB], const int (&z)[NB],
+                                                int n, float* sc, unsigned mask, int g, const uint8_t* ex,
+                                                const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+#pragma unroll
+    for (int k = 0; k < NB; k++)
+        if (k < n) stv<V>(sc + k * Q + g * V, x[k]);
+    __syncwarp(mask);
+#pragma unroll
+    for (int k = 0; k < NB; k++) {
+        if (k < n) {
+#pragma unroll
+            for (int v = 0; v < V; v++) x[k][v] = sc[k * Q + ((z[k] ^ gf_mul(ex, lg, h[k], g * V + v)) & (Q - 1))];
+        }
+    }
+    __syncwarp(mask);
+#pragma unroll
+    for (int k = 0; k < NB; k++)
+        if (k < n) gnormalise<Q>(x[k], mask);
+}
+
 // p_j: normalised channel likelihood times the block prior of a source symbol.
 template <int Q>
 __device__ __forceinline__ void prior_vec(const DecodeArgs& A, int f, int j, float (&x)[Lay<Q>::V], unsigned mask,
@@ -468,6 +556,10 @@ __device__ __forceinline__ void markov_prior(const DecodeArgs& A, int f, int i, 
 }
 
 // Launchers (one instantiation set per schedule, see pus.cu / sus.cu).
+// Check-node arithmetic: probability-domain convolution (q <= 16) or the
+// deviation transform (any q).
+enum Method { kDirect = 0, kTransform = 1 };
+
 cudaError_t launch_channel(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);

@@ -68,8 +68,79 @@ __device__ __forceinline__ void pus_check(const DecodeArgs& A, float* slab, int 
     }
 }
 
+// r_ij for every edge of check i by the probability-domain route: suffix
+// convolutions S_k = qt_{k+1} * ... * qt_{d-1}, a running prefix P, and
+// r_k from P * S_k (3(d-2) convolutions for d edges).  The group's scratch
+// holds the d stored vectors and two operand slots.
+template <int Q, int DC>
+__device__ __forceinline__ void pus_check_direct(const DecodeArgs& A, float* slab, int f, int i, float* sc,
+                                                 unsigned mask, int g, const uint8_t* ex, const uint8_t* lg) {
+    constexpr int V = Lay<Q>::V;
+    const int e0 = A.c.rowptr[i];
+    const int d = A.c.rowptr[i + 1] - e0;
+    const int z = A.syn ? (A.syn[(size_t)f * A.c.M + i] & (Q - 1)) : 0;
+    float* T0 = sc + DC * Q;
+    float* T1 = T0 + Q;
+#pragma unroll
+    for (int k = 0; k < DC; k++) {
+        if (k < d) {
+            float x[V];
+            ldv<V>(x, slab + (size_t)(e0 + k) * Q + g * V);
+            stv<V>(sc + k * Q + g * V, x);
+        }
+    }
+    __syncwarp(mask);
+    float S[DC][V];  // S[k] = qt_{k+1} * ... * qt_{d-1} for k <= d-2
+#pragma unroll
+    for (int k = DC - 2; k >= 0; k--) {
+        if (k == d - 2) {
+            ldv<V>(S[k], sc + (k + 1) * Q + g * V);
+        } else if (k < d - 2) {
+            stv<V>(T0 + g * V, S[k + 1]);
+            __syncwarp(mask);
+            xconv_sm<Q>(S[k], T0, sc + (k + 1) * Q, g);
+            __syncwarp(mask);
+        }
+    }
+    float P[V];
+    bool p_id = true;  // P is the identity (no edge folded in yet)
+#pragma unroll
+    for (int k = 0; k < DC; k++) {
+        if (k < d) {
+            float out[1][V];
+            if (k == d - 1) {
+#pragma unroll
+                for (int v = 0; v < V; v++) out[0][v] = p_id ? ((g * V + v) == 0 ? 1.f : 0.f) : P[v];
+            } else if (p_id) {
+#pragma unroll
+                for (int v = 0; v < V; v++) out[0][v] = S[k][v];
+            } else {
+                stv<V>(T0 + g * V, P);
+                stv<V>(T1 + g * V, S[k]);
+                __syncwarp(mask);
+                xconv_sm<Q>(out[0], T0, T1, g);
+                __syncwarp(mask);
+            }
+            if (k < d - 1) {
+                if (p_id) {
+                    ldv<V>(P, sc + k * Q + g * V);
+                    p_id = false;
+                } else {
+                    stv<V>(T0 + g * V, P);
+                    __syncwarp(mask);
+                    xconv_sm<Q>(P, T0, sc + k * Q, g);
+                    __syncwarp(mask);
+                }
+            }
+            const int hh[1] = {A.c.eh[e0 + k]}, zz[1] = {z};
+            direct_finish_n<Q, 1>(out, hh, zz, 1, T1, mask, g, ex, lg);
+            stv<V>(slab + (size_t)(e0 + k) * Q + g * V, out[0]);
+        }
+    }
+}
+
 // q_ij for every edge of column j (Eq. 4), Q_j (Eq. 5) and its hard decision.
-template <int Q, int DV>
+template <int Q, int DV, int METHOD>
 __device__ __forceinline__ void pus_var(const DecodeArgs& A, float* slab, int f, int j, float* sc, unsigned mask,
                                         int g, const uint8_t* ex, const uint8_t* lg) {
     constexpr int V = Lay<Q>::V;
@@ -122,26 +193,36 @@ __device__ __forceinline__ void pus_var(const DecodeArgs& A, float* slab, int f,
             }
             gnormalise<Q>(x, mask);
             if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + e) * Q + g * V, x);
-            to_deviation<Q>(x, A.c.eh[e], sc, mask, g, ex, lg);
+            if constexpr (METHOD == kDirect) to_relabelled<Q>(x, A.c.eh[e], sc, mask, g, ex, lg);
+            else to_deviation<Q>(x, A.c.eh[e], sc, mask, g, ex, lg);
             stv<V>(slab + (size_t)e * Q + g * V, x);
         }
     }
 }
 
-template <int Q, int DC, int DV>
+// Per-group scratch floats: one vector (transform route) or the check's d
+// stored vectors plus two operands (probability route); +4 floats of padding
+// spread the groups over the shared-memory banks.
+template <int Q, int DC, int METHOD>
+constexpr int pus_group_scratch() {
+    return (METHOD == kDirect ? (DC + 2) * Q : Q) + 4;
+}
+
+template <int Q, int DC, int DV, int METHOD>
 __global__ void __launch_bounds__(kPusThreads) k_pus(const DecodeArgs A) {
     constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+    constexpr int SCR = pus_group_scratch<Q, DC, METHOD>();
     __shared__ uint8_t s_exp[512];
     __shared__ uint8_t s_log[256];
-    __shared__ __align__(16) float s_scr[kPusThreads * V];
     __shared__ int s_frame;
+    extern __shared__ __align__(16) float s_scr[];
 
     const int tid = threadIdx.x;
     const int g = tid & (G - 1);
     const int grp = tid / G;
     const int ngrp = blockDim.x / G;
     const unsigned mask = group_mask<G>();
-    float* sc = s_scr + grp * Q;
+    float* sc = s_scr + grp * SCR;
     for (int k = tid; k < 512; k += blockDim.x) s_exp[k] = A.c.gexp[k];
     for (int k = tid; k < 256; k += blockDim.x) s_log[k] = A.c.glog[k];
     const int M = A.c.M, N = A.c.N;
@@ -155,7 +236,7 @@ __global__ void __launch_bounds__(kPusThreads) k_pus(const DecodeArgs A) {
         if (f >= A.F) break;
         float* slab = A.msg + (size_t)f * E * Q;
 
-        // q_ij <- p_j (Sec. 2) or the caller's state, stored as transforms
+        // q_ij <- p_j (Sec. 2) or the caller's state, in stored form
         for (long long e = grp; e < E; e += ngrp) {
             float x[V];
             if (A.step) {
@@ -163,16 +244,20 @@ __global__ void __launch_bounds__(kPusThreads) k_pus(const DecodeArgs A) {
             } else {
                 prior_vec<Q>(A, f, A.c.ecol[e], x, mask, g);
             }
-            to_deviation<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+            if constexpr (METHOD == kDirect) to_relabelled<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+            else to_deviation<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
             stv<V>(slab + (size_t)e * Q + g * V, x);
         }
         __syncthreads();
 
         int t = 1, ok = 0;
         for (;; t++) {
-            for (int i = grp; i < M; i += ngrp) pus_check<Q, DC>(A, slab, f, i, sc, mask, g, s_exp, s_log);
+            for (int i = grp; i < M; i += ngrp) {
+                if constexpr (METHOD == kDirect) pus_check_direct<Q, DC>(A, slab, f, i, sc, mask, g, s_exp, s_log);
+                else pus_check<Q, DC>(A, slab, f, i, sc, mask, g, s_exp, s_log);
+            }
             __syncthreads();
-            for (int j = grp; j < N; j += ngrp) pus_var<Q, DV>(A, slab, f, j, sc, mask, g, s_exp, s_log);
+            for (int j = grp; j < N; j += ngrp) pus_var<Q, DV, METHOD>(A, slab, f, j, sc, mask, g, s_exp, s_log);
             __syncthreads();
             int bad = 0;
             for (int i = tid; i < M; i += blockDim.x) {
@@ -209,39 +294,52 @@ __global__ void __launch_bounds__(kPusThreads) k_pus(const DecodeArgs A) {
     }
 }
 
-template <int Q, int DC, int DV>
+template <int Q, int DC, int DV, int METHOD>
 cudaError_t launch_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    constexpr int G = Lay<Q>::G;
+    constexpr size_t smem = sizeof(float) * (size_t)(kPusThreads / G) * pus_group_scratch<Q, DC, METHOD>();
     static int occ = -1;
     if (occ < 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus<Q, DC, DV>, kPusThreads, 0);
+        cudaError_t e = cudaFuncSetAttribute(k_pus<Q, DC, DV, METHOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus<Q, DC, DV, METHOD>, kPusThreads, smem);
         if (e != cudaSuccess) return e;
         if (occ < 1) occ = 1;
     }
     long long grid = (long long)num_sms * occ;
     if (grid > A.F) grid = A.F;
     if (grid < 1) return cudaSuccess;
-    k_pus<Q, DC, DV><<<(int)grid, kPusThreads, 0, s>>>(A);
+    k_pus<Q, DC, DV, METHOD><<<(int)grid, kPusThreads, smem, s>>>(A);
     return cudaGetLastError();
 }
 
-template <int Q>
+template <int Q, int METHOD>
 cudaError_t launch_deg(const DecodeArgs& A, int num_sms, cudaStream_t s) {
-    if (A.c.dcmax <= 6 && A.c.dvmax <= 3) return launch_q<Q, 6, 3>(A, num_sms, s);
-    return launch_q<Q, 16, 8>(A, num_sms, s);
+    if (A.c.dcmax <= 6 && A.c.dvmax <= 3) return launch_q<Q, 6, 3, METHOD>(A, num_sms, s);
+    return launch_q<Q, 16, 8, METHOD>(A, num_sms, s);
+}
+
+template <int Q>
+cudaError_t launch_method(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    if constexpr (Q <= 16) {
+        if (A.method == kDirect) return launch_deg<Q, kDirect>(A, num_sms, s);
+    }
+    return launch_deg<Q, kTransform>(A, num_sms, s);
 }
 
 }  // namespace
 
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     switch (A.c.q) {
-    case 2: return launch_deg<2>(A, num_sms, s);
-    case 4: return launch_deg<4>(A, num_sms, s);
-    case 8: return launch_deg<8>(A, num_sms, s);
-    case 16: return launch_deg<16>(A, num_sms, s);
-    case 32: return launch_deg<32>(A, num_sms, s);
-    case 64: return launch_deg<64>(A, num_sms, s);
-    case 128: return launch_deg<128>(A, num_sms, s);
-    case 256: return launch_deg<256>(A, num_sms, s);
+    case 2: return launch_method<2>(A, num_sms, s);
+    case 4: return launch_method<4>(A, num_sms, s);
+    case 8: return launch_method<8>(A, num_sms, s);
+    case 16: return launch_method<16>(A, num_sms, s);
+    case 32: return launch_method<32>(A, num_sms, s);
+    case 64: return launch_method<64>(A, num_sms, s);
+    case 128: return launch_method<128>(A, num_sms, s);
+    case 256: return launch_method<256>(A, num_sms, s);
     }
     return cudaErrorInvalidValue;
 }

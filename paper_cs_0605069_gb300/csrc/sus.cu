@@ -49,14 +49,17 @@ __device__ __forceinline__ void load_col(ColBuf<Q, DC, DV>& b, const DecodeArgs&
 
 // Steps 1-2 for column j once E (the combined other-edge vectors) and C (the
 // XOR of their shifts) are known for each of the column's d checks.
-template <int Q, int DV>
+template <int Q, int DV, int METHOD>
 __device__ __forceinline__ void sus_column_tail(const DecodeArgs& A, float* slab, int f, int j, int d,
                                                 float (&E)[DV][Lay<Q>::V], const int (&C)[DV], const int (&eid)[DV],
                                                 const int (&h)[DV], const int (&z)[DV], uint8_t* xh, float* sc,
                                                 unsigned mask, int g, const uint8_t* ex, const uint8_t* lg) {
     constexpr int V = Lay<Q>::V;
     const int N = A.c.N;
-    dev_finish_n<Q, DV>(E, C, h, z, d, sc, mask, g, ex, lg);  // E now holds r_ij
+    // E: transform route, the combined deviations; probability route, the
+    // distribution of the other edges' sum.  Afterwards E holds r_ij.
+    if constexpr (METHOD == kDirect) direct_finish_n<Q, DV>(E, h, z, d, sc, mask, g, ex, lg);
+    else dev_finish_n<Q, DV>(E, C, h, z, d, sc, mask, g, ex, lg);
     float p[V];
     prior_vec<Q>(A, f, j, p, mask, g);
     float S[DV][V], acc[V];
@@ -106,27 +109,80 @@ __device__ __forceinline__ void sus_column_tail(const DecodeArgs& A, float* slab
             if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + eid[k]) * Q + g * V, E[k]);
         }
     }
-    to_deviation_n<Q, DV>(E, h, d, sc, mask, g, ex, lg);
+    if constexpr (METHOD == kDirect) to_relabelled_n<Q, DV>(E, h, d, sc, mask, g, ex, lg);
+    else to_deviation_n<Q, DV>(E, h, d, sc, mask, g, ex, lg);
 #pragma unroll
     for (int k = 0; k < DV; k++)
         if (k < d) stv<V>(slab + (size_t)eid[k] * Q + g * V, E[k]);
 }
 
-template <int Q, int DC, int DV>
+// Fold the stored vector y of one more neighbour into check k's accumulator:
+// transform route, E <- E + y (1 - E) and the shift XOR; probability route,
+// U <- U * y (convolution) in shared memory, batched over the column's checks.
+template <int Q, int DV, int METHOD>
+__device__ __forceinline__ void fold_round(float (&U)[DV][Lay<Q>::V], int (&C)[DV], bool (&started)[DV],
+                                           float (&Y)[DV][Lay<Q>::V], const bool (&take)[DV], float* sc,
+                                           unsigned mask, int g) {
+    constexpr int V = Lay<Q>::V;
+    if constexpr (METHOD == kTransform) {
+#pragma unroll
+        for (int k = 0; k < DV; k++) {
+            if (take[k]) {
+                if (g == 0) {
+                    C[k] ^= (int)Y[k][0];
+                    Y[k][0] = 0.f;
+                }
+                dev_combine<V>(U[k], Y[k]);
+                started[k] = true;
+            }
+        }
+    } else {
+        bool conv[DV];
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < DV; k++) {
+            conv[k] = take[k] && started[k];
+            if (take[k] && !started[k]) {
+#pragma unroll
+                for (int v = 0; v < V; v++) U[k][v] = Y[k][v];
+                started[k] = true;
+            }
+            any |= conv[k];
+        }
+        if (any) {
+#pragma unroll
+            for (int k = 0; k < DV; k++) {
+                if (conv[k]) {
+                    stv<V>(sc + (2 * k) * Q + g * V, U[k]);
+                    stv<V>(sc + (2 * k + 1) * Q + g * V, Y[k]);
+                }
+            }
+            __syncwarp(mask);
+#pragma unroll
+            for (int k = 0; k < DV; k++)
+                if (conv[k]) xconv_sm<Q>(U[k], sc + (2 * k) * Q, sc + (2 * k + 1) * Q, g);
+            __syncwarp(mask);
+        }
+    }
+}
+
+template <int Q, int DC, int DV, int METHOD>
 __global__ void __launch_bounds__(kSusThreads) k_sus(const DecodeArgs A) {
     constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
     // keep both column buffers in registers only while they are small
     constexpr bool PF = (2 * DV * DC * V <= 160);
+    // per group: one (transform) or two (probability route) vector slots per check, + bank padding
+    constexpr int SCR = (METHOD == kDirect ? 2 : 1) * DV * Q + 4;
     __shared__ uint8_t s_exp[512];
     __shared__ uint8_t s_log[256];
-    __shared__ __align__(16) float s_scr[kSusThreads * V * DV];
+    __shared__ __align__(16) float s_scr[(kSusThreads / G) * SCR];
 
     const int tid = threadIdx.x;
     const int g = tid & (G - 1);
     const int grp = tid / G;
     const unsigned mask = group_mask<G>();
     const int lane0 = (threadIdx.x & 31) & ~(G - 1);
-    float* sc = s_scr + grp * Q * DV;
+    float* sc = s_scr + grp * SCR;
     for (int k = tid; k < 512; k += blockDim.x) s_exp[k] = A.c.gexp[k];
     for (int k = tid; k < 256; k += blockDim.x) s_log[k] = A.c.glog[k];
     __syncthreads();
@@ -144,76 +200,73 @@ __global__ void __launch_bounds__(kSusThreads) k_sus(const DecodeArgs A) {
 
         int t = 1, ok = 0;
         for (;; t++) {
-            if constexpr (PF) {
-                ColBuf<Q, DC, DV> cur, nxt;
-                load_col<Q, DC, DV>(cur, A, slab, 0, g);
-                for (int j = 0; j < N; j++) {
+            ColBuf<Q, PF ? DC : 1, PF ? DV : 1> cur, nxt;
+            if constexpr (PF) load_col<Q, DC, DV>(cur, A, slab, 0, g);
+            for (int j = 0; j < N; j++) {
+                if constexpr (PF) {
                     if (j + 1 < N) load_col<Q, DC, DV>(nxt, A, slab, j + 1, g);
-                    const int d = cur.d;
-                    float Ek[DV][V];
-                    int C[DV], eid[DV], h[DV], z[DV];
+                }
+                const int c0 = A.c.colptr[j];
+                const int d = A.c.colptr[j + 1] - c0;
+                int4 info[DV];
+                float U[DV][V];
+                int C[DV], eid[DV], h[DV], z[DV], own[DV], dc[DV];
+                bool started[DV];
+#pragma unroll
+                for (int k = 0; k < DV; k++) {
+                    C[k] = 0;
+                    started[k] = false;
+#pragma unroll
+                    for (int v = 0; v < V; v++) U[k][v] = 0.f;
+                    if constexpr (PF) info[k] = cur.info[k];
+                    else info[k] = (k < d) ? A.c.cinfo[c0 + k] : make_int4(0, 0, 0, 0);
+                    if (k < d) {
+                        eid[k] = info[k].x;
+                        h[k] = (info[k].z >> 8) & 255;
+                        z[k] = zf ? (zf[info[k].w] & (Q - 1)) : 0;
+                        own[k] = info[k].x - info[k].y;
+                        dc[k] = info[k].z & 255;
+                    } else {
+                        eid[k] = 0; h[k] = 1; z[k] = 0; own[k] = -1; dc[k] = 0;
+                    }
+                }
+                // step 1: fold every other edge of each check of column j
+#pragma unroll
+                for (int m = 0; m < DC; m++) {
+                    float Y[DV][V];
+                    bool take[DV];
 #pragma unroll
                     for (int k = 0; k < DV; k++) {
-                        C[k] = 0;
+                        take[k] = (k < d) && (m < dc[k]) && (m != own[k]);
+                        if (take[k]) {
+                            if constexpr (PF) {
 #pragma unroll
-                        for (int v = 0; v < V; v++) Ek[k][v] = 0.f;
-                        if (k < d) {
-                            const int4 in = cur.info[k];
-                            eid[k] = in.x;
-                            h[k] = (in.z >> 8) & 255;
-                            z[k] = zf ? (zf[in.w] & (Q - 1)) : 0;
-                            const int own = in.x - in.y, dc = in.z & 255;
-#pragma unroll
-                            for (int m = 0; m < DC; m++) {
-                                if (m < dc && m != own) {
-                                    if (g == 0) {
-                                        C[k] ^= (int)cur.D[k][m][0];
-                                        cur.D[k][m][0] = 0.f;
-                                    }
-                                    dev_combine<V>(Ek[k], cur.D[k][m]);
-                                }
+                                for (int v = 0; v < V; v++) Y[k][v] = cur.D[k][m][v];
+                            } else {
+                                ldv<V>(Y[k], slab + (size_t)(info[k].y + m) * Q + g * V);
                             }
-                        } else {
-                            eid[k] = 0; h[k] = 1; z[k] = 0;
                         }
+                    }
+                    fold_round<Q, DV, METHOD>(U, C, started, Y, take, sc, mask, g);
+                }
+#pragma unroll
+                for (int k = 0; k < DV; k++) {
+                    if constexpr (METHOD == kDirect) {
+                        if (k < d && !started[k]) {   // no other edge: y = 0 with certainty
+#pragma unroll
+                            for (int v = 0; v < V; v++) U[k][v] = (g * V + v) == 0 ? 1.f : 0.f;
+                        }
+                    } else {
                         C[k] = __shfl_sync(mask, C[k], lane0);
                     }
-                    sus_column_tail<Q, DV>(A, slab, f, j, d, Ek, C, eid, h, z, xh, sc, mask, g, s_exp, s_log);
+                }
+                // step 2: q_ij for column j, and Q_j
+                sus_column_tail<Q, DV, METHOD>(A, slab, f, j, d, U, C, eid, h, z, xh, sc, mask, g, s_exp, s_log);
+                if constexpr (PF) {
                     if (j + 1 < N) {
                         if (A.c.cdep[j + 1]) load_col<Q, DC, DV>(nxt, A, slab, j + 1, g);
                         cur = nxt;
                     }
-                }
-            } else {
-                for (int j = 0; j < N; j++) {
-                    const int c0 = A.c.colptr[j];
-                    const int d = A.c.colptr[j + 1] - c0;
-                    float Ek[DV][V];
-                    int C[DV], eid[DV], h[DV], z[DV];
-#pragma unroll
-                    for (int k = 0; k < DV; k++) {
-                        C[k] = 0;
-#pragma unroll
-                        for (int v = 0; v < V; v++) Ek[k][v] = 0.f;
-                        eid[k] = 0; h[k] = 1; z[k] = 0;
-                        if (k < d) {
-                            const int4 in = A.c.cinfo[c0 + k];
-                            eid[k] = in.x;
-                            h[k] = (in.z >> 8) & 255;
-                            z[k] = zf ? (zf[in.w] & (Q - 1)) : 0;
-                            const int e0 = in.y, dc = in.z & 255;
-                            for (int m = 0; m < dc; m++) {
-                                if (e0 + m == in.x) continue;
-                                float D[V];
-                                int c;
-                                ld_dev<V>(D, c, slab + (size_t)(e0 + m) * Q + g * V, g);
-                                C[k] ^= c;
-                                dev_combine<V>(Ek[k], D);
-                            }
-                        }
-                        C[k] = __shfl_sync(mask, C[k], lane0);
-                    }
-                    sus_column_tail<Q, DV>(A, slab, f, j, d, Ek, C, eid, h, z, xh, sc, mask, g, s_exp, s_log);
                 }
             }
             __syncwarp(mask);
@@ -255,7 +308,7 @@ __global__ void __launch_bounds__(kSusThreads) k_sus(const DecodeArgs A) {
 
 // q_ij <- p_j (Sec. 2 initialisation) or the caller's state, in stored form,
 // one lane group per (frame, edge).
-template <int Q>
+template <int Q, int METHOD>
 __global__ void __launch_bounds__(256) k_init_dev(const DecodeArgs A) {
     constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
     __shared__ uint8_t s_exp[512];
@@ -277,18 +330,19 @@ __global__ void __launch_bounds__(256) k_init_dev(const DecodeArgs A) {
         float x[V];
         if (A.step) ldv<V>(x, A.msg_io + (size_t)it * Q + g * V);
         else prior_vec<Q>(A, f, A.c.ecol[e], x, mask, g);
-        to_deviation<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+        if constexpr (METHOD == kDirect) to_relabelled<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+        else to_deviation<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
         stv<V>(A.msg + (size_t)it * Q + g * V, x);
     }
 }
 
-template <int Q, int DC, int DV>
+template <int Q, int DC, int DV, int METHOD>
 cudaError_t launch_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr int G = Lay<Q>::G;
     constexpr int groups_per_block = kSusThreads / G;
     static int occ = -1;
     if (occ < 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus<Q, DC, DV>, kSusThreads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus<Q, DC, DV, METHOD>, kSusThreads, 0);
         if (e != cudaSuccess) return e;
         if (occ < 1) occ = 1;
     }
@@ -296,14 +350,22 @@ cudaError_t launch_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     long long cap = (long long)num_sms * occ;
     long long grid = want < cap ? want : cap;
     if (grid < 1) return cudaSuccess;
-    k_sus<Q, DC, DV><<<(int)grid, kSusThreads, 0, s>>>(A);
+    k_sus<Q, DC, DV, METHOD><<<(int)grid, kSusThreads, 0, s>>>(A);
     return cudaGetLastError();
 }
 
-template <int Q>
+template <int Q, int METHOD>
 cudaError_t launch_deg(const DecodeArgs& A, int num_sms, cudaStream_t s) {
-    if (A.c.dcmax <= 6 && A.c.dvmax <= 3) return launch_q<Q, 6, 3>(A, num_sms, s);
-    return launch_q<Q, 16, 8>(A, num_sms, s);
+    if (A.c.dcmax <= 6 && A.c.dvmax <= 3) return launch_q<Q, 6, 3, METHOD>(A, num_sms, s);
+    return launch_q<Q, 16, 8, METHOD>(A, num_sms, s);
+}
+
+template <int Q>
+cudaError_t launch_method(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    if constexpr (Q <= 16) {
+        if (A.method == kDirect) return launch_deg<Q, kDirect>(A, num_sms, s);
+    }
+    return launch_deg<Q, kTransform>(A, num_sms, s);
 }
 
 template <int Q>
@@ -313,7 +375,13 @@ cudaError_t launch_init_q(const DecodeArgs& A, cudaStream_t s) {
     long long blocks = (total + (256 / G) - 1) / (256 / G);
     if (blocks > 65535LL * 16) blocks = 65535LL * 16;
     if (blocks < 1) return cudaSuccess;
-    k_init_dev<Q><<<(unsigned)blocks, 256, 0, s>>>(A);
+    if constexpr (Q <= 16) {
+        if (A.method == kDirect) {
+            k_init_dev<Q, kDirect><<<(unsigned)blocks, 256, 0, s>>>(A);
+            return cudaGetLastError();
+        }
+    }
+    k_init_dev<Q, kTransform><<<(unsigned)blocks, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -321,14 +389,14 @@ cudaError_t launch_init_q(const DecodeArgs& A, cudaStream_t s) {
 
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     switch (A.c.q) {
-    case 2: return launch_deg<2>(A, num_sms, s);
-    case 4: return launch_deg<4>(A, num_sms, s);
-    case 8: return launch_deg<8>(A, num_sms, s);
-    case 16: return launch_deg<16>(A, num_sms, s);
-    case 32: return launch_deg<32>(A, num_sms, s);
-    case 64: return launch_deg<64>(A, num_sms, s);
-    case 128: return launch_deg<128>(A, num_sms, s);
-    case 256: return launch_deg<256>(A, num_sms, s);
+    case 2: return launch_method<2>(A, num_sms, s);
+    case 4: return launch_method<4>(A, num_sms, s);
+    case 8: return launch_method<8>(A, num_sms, s);
+    case 16: return launch_method<16>(A, num_sms, s);
+    case 32: return launch_method<32>(A, num_sms, s);
+    case 64: return launch_method<64>(A, num_sms, s);
+    case 128: return launch_method<128>(A, num_sms, s);
+    case 256: return launch_method<256>(A, num_sms, s);
     }
     return cudaErrorInvalidValue;
 }

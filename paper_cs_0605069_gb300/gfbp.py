@@ -21,6 +21,7 @@ _lock = threading.Lock()
 GFBP_OK, GFBP_EINVAL, GFBP_ENOMEM, GFBP_ECUDA, GFBP_ETIMEOUT, GFBP_EBUSY, GFBP_EUNSUPPORTED = range(7)
 CHANNEL = {"bsc": 0, "bec": 1, "awgn": 2, "biawgn": 2, "loglik": 3}
 SCHEDULE = {"pus": 0, "sus": 1}
+CHECK_METHOD = {"auto": 0, "transform": 1, "direct": 2}
 
 # Functions declared in include/gfbp.h (the CPU test checks that every one is exported).
 EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info",
@@ -44,7 +45,7 @@ class gfbp_prior(C.Structure):
 class gfbp_options(C.Structure):
     _fields_ = [("punct", C.c_void_p), ("syndrome", C.c_void_p), ("post", C.c_void_p),
                 ("xhat_trace", C.c_void_p), ("no_early_stop", C.c_int32), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t), ("kernel_events", C.c_void_p * 2)]
+                ("workspace_bytes", C.c_size_t), ("kernel_events", C.c_void_p * 2), ("check_method", C.c_int32)]
 
 
 def lib() -> C.CDLL:
@@ -149,7 +150,7 @@ def workspace_size(code: Code, n_frames: int, schedule: str = "pus", T=None, K: 
 def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: str = "pus", max_iter: int = 100,
            T=None, K: int = 0, src_pos=None, frame_param=None, punct=None, syndrome=None, post: bool = False,
            trace: bool = False, no_early_stop: bool = False, workspace=None, out=None, stream=None,
-           kernel_events=None):
+           kernel_events=None, check_method: str = "auto"):
     """gfbp_decode on CUDA tensors.  obs: float32 [F][N][p] (or [F][N][q] for
     loglik).  Returns dict of device tensors x_hat [F][N] uint8, iters [F]
     int32, converged [F] uint8 (+ post [F][N][q], trace [F][max_iter][N])."""
@@ -170,7 +171,11 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     opt = gfbp_options(_ptr(punct), _ptr(syndrome), _ptr(out.get("post")), _ptr(out.get("trace")),
                        int(no_early_stop), _ptr(workspace), int(workspace.numel()))
+    opt.check_method = CHECK_METHOD[check_method]
     if kernel_events is not None:   # (torch.cuda.Event, torch.cuda.Event) timing the schedule kernel alone
+        for ev in kernel_events:    # torch creates the CUDA event on its first record
+            if not ev.cuda_event:
+                ev.record(stream if stream is not None else torch.cuda.current_stream())
         opt.kernel_events[0] = kernel_events[0].cuda_event
         opt.kernel_events[1] = kernel_events[1].cuda_event
     ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
@@ -181,7 +186,8 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
 
 
 def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedule: str = "pus", T=None, K: int = 0,
-         src_pos=None, prior_in=None, frame_param=None, punct=None, syndrome=None, stream=None):
+         src_pos=None, prior_in=None, frame_param=None, punct=None, syndrome=None, stream=None,
+         check_method: str = "auto"):
     """gfbp_step: one iteration from msg (float32 [F][E][q], updated in place).
     Returns dict(msg, post, x_hat, sat, prior_out)."""
     import torch
@@ -194,6 +200,7 @@ def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedul
     pr, _keep = _prior(T, K, src_pos)
     ws = torch.empty(workspace_size(code, F, schedule, T, K, src_pos, step=True), dtype=torch.uint8, device=dev)
     opt = gfbp_options(_ptr(punct), _ptr(syndrome), None, None, 0, _ptr(ws), int(ws.numel()))
+    opt.check_method = CHECK_METHOD[check_method]
     ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
     _ok(lib().gfbp_step(code.handle, F, _ptr(obs), ch, SCHEDULE[schedule], C.byref(pr), _ptr(msg), _ptr(prior_in),
                         _ptr(prior_out), _ptr(post), _ptr(x_hat), _ptr(sat), C.byref(opt), _stream(stream)),

@@ -18,7 +18,7 @@ def to_dev(a, dtype=None):
 
 
 def gpu_decode(code_dev, obs, channel, param, schedule, max_iter, T=None, K=0, src_pos=None, punct=None,
-               syndrome=None, trace=False, post=False, no_early_stop=False):
+               syndrome=None, trace=False, post=False, no_early_stop=False, check_method="auto"):
     import torch
     from paper_cs_0605069_gb300 import gfbp
     fp = np.asarray(param, np.float32)
@@ -27,32 +27,63 @@ def gpu_decode(code_dev, obs, channel, param, schedule, max_iter, T=None, K=0, s
                       schedule=schedule, max_iter=max_iter, T=T, K=K, src_pos=src_pos, frame_param=frame_param,
                       punct=None if punct is None else to_dev(punct),
                       syndrome=None if syndrome is None else to_dev(syndrome), post=post, trace=trace,
-                      no_early_stop=no_early_stop)
+                      no_early_stop=no_early_stop, check_method=check_method)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-def classify_frames(gpu, ora, gap_thr=TIE_GAP):
+# Relative perturbation of the channel parameter used to find each frame's
+# conditioning horizon (about ten FP32 ulps, the size of the rounding the
+# device path adds to every message).
+HORIZON_REL = 1e-6
+
+
+def oracle_horizon(oracle, code, obs, kind, param, schedule, max_iter, gap_thr=TIE_GAP, **kw):
+    """Per frame, the first iteration at which the oracle's own hard decisions
+    change (on a symbol with top-two gap > gap_thr) when the channel parameter
+    is perturbed by HORIZON_REL; max_iter + 1 when they never do.  Beyond it
+    the frame's trajectory is not determined to FP32 precision (BP past the
+    code's threshold iterates chaotically), so no FP32 result can follow it."""
+    a = oracle.decode(code, obs, kind, param, schedule, max_iter=max_iter, trace=True, early_stop=False, **kw)
+    prm = np.asarray(param, np.float64) * (1.0 + HORIZON_REL)
+    if kind == "loglik":
+        obs = np.asarray(obs, np.float32) * np.float32(1.0 + HORIZON_REL)
+    b = oracle.decode(code, obs, kind, prm, schedule, max_iter=max_iter, trace=True, early_stop=False, **kw)
+    bad = (a["trace_x"] != b["trace_x"]) & (a["trace_gap"] > gap_thr)
+    F = bad.shape[0]
+    hz = np.full(F, max_iter + 1, np.int64)
+    for f in range(F):
+        t = np.nonzero(bad[f].any(1))[0]
+        if t.size:
+            hz[f] = int(t[0]) + 1
+    return hz
+
+
+def classify_frames(gpu, ora, gap_thr=TIE_GAP, horizon=None):
     """Per frame: 'match' (identical decisions, count and flag), 'tie' (every
     per-iteration hard-decision disagreement up to the earlier stop sits on a
-    symbol whose oracle top-two gap <= gap_thr) or 'fail'."""
+    symbol whose oracle top-two gap <= gap_thr), 'horizon' (the frame runs past
+    its conditioning horizon and the decisions agree, ties aside, before it)
+    or 'fail'."""
     F = len(ora["iters"])
     kinds = []
     for f in range(F):
         same = (gpu["iters"][f] == ora["iters"][f] and gpu["converged"][f] == ora["conv"][f]
                 and (gpu["x_hat"][f] == ora["xhat"][f]).all())
         tmax = int(min(gpu["iters"][f], ora["iters"][f]))
-        tg = gpu["trace"][f, :tmax]
-        to = ora["trace_x"][f, :tmax]
-        gap = ora["trace_gap"][f, :tmax]
+        hz = int(horizon[f]) if horizon is not None else 10 ** 9
+        tcmp = min(tmax, hz - 1)
+        tg = gpu["trace"][f, :tcmp]
+        to = ora["trace_x"][f, :tcmp]
+        gap = ora["trace_gap"][f, :tcmp]
         dis = tg != to
-        if not dis.any() and same:
+        clean = (not dis.any()) or (gap[dis] <= gap_thr).all()
+        if same and not dis.any():
             kinds.append("match")
-        elif dis.any() and (gap[dis] <= gap_thr).all():
+        elif clean and tmax < hz and dis.any():
             kinds.append("tie")
-        elif not dis.any():
-            # identical decisions up to the earlier stop but different stops
-            kinds.append("fail")
+        elif clean and max(gpu["iters"][f], ora["iters"][f]) >= hz:
+            kinds.append("horizon")
         else:
             kinds.append("fail")
     return np.array(kinds)
