@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--schedules", default="pus,sus", help="comma list (profiling cases)")
+    ap.add_argument("--max-iter", type=int, default=0, help="override the workload's max_iter (profiling cases)")
+    ap.add_argument("--method", default="auto", choices=["auto", "direct", "transform"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -201,7 +204,8 @@ def main():
     dev = torch.device("cuda", local)
     obs = torch.from_numpy(b.obs).to(dev)
     sig = torch.from_numpy(b.param.astype(np.float32)).to(dev)
-    scheds = ("pus", "sus")
+    scheds = tuple(args.schedules.split(","))
+    max_iter = args.max_iter or b.max_iter
     ws = {s: torch.empty(gfbp.workspace_size(code, F, s), dtype=torch.uint8, device=dev) for s in scheds}
     outs = {s: dict(x_hat=torch.empty((F, N), dtype=torch.uint8, device=dev),
                     iters=torch.empty(F, dtype=torch.int32, device=dev),
@@ -212,8 +216,8 @@ def main():
     def step(record=None):
         for s in scheds:
             ev = record[s] if record else None
-            gfbp.decode(code, obs, "awgn", 0.0, schedule=s, max_iter=b.max_iter, frame_param=sig,
-                        workspace=ws[s], out=outs[s], kernel_events=ev)
+            gfbp.decode(code, obs, "awgn", 0.0, schedule=s, max_iter=max_iter, frame_param=sig,
+                        workspace=ws[s], out=outs[s], kernel_events=ev, check_method=args.method)
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -246,7 +250,7 @@ def main():
         total_ms = float(t.item())
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
-    frames_per_step = 2 * F * world
+    frames_per_step = len(scheds) * F * world
     value = frames_per_step / (ms_per_step / 1e3)
 
     # end to end through the public API: pinned host obs in, results out, every step
@@ -264,8 +268,8 @@ def main():
             obs_d.copy_(host_obs, non_blocking=True)
             sig_d.copy_(host_sig, non_blocking=True)
             for s in scheds:
-                gfbp.decode(code, obs_d, "awgn", 0.0, schedule=s, max_iter=b.max_iter, frame_param=sig_d,
-                            workspace=ws[s], out=outs[s])
+                gfbp.decode(code, obs_d, "awgn", 0.0, schedule=s, max_iter=max_iter, frame_param=sig_d,
+                            workspace=ws[s], out=outs[s], check_method=args.method)
                 for k in outs[s]:
                     host_out[s][k].copy_(outs[s][k], non_blocking=True)
 
@@ -304,6 +308,7 @@ def main():
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     symit_launch = float(np.stack(iters[dom]).sum()) * N / args.steps
+    q_alg = ALG_BYTES_PER_SYMITER[dom]
     alg_bytes = ALG_BYTES_PER_SYMITER[dom] * q * symit_launch
     achieved = alg_bytes / (per[dom]["kernel_ms"] / 1e3) / 1e9
     traffic = profiled_traffic("k_" + dom, symit_launch)
@@ -311,22 +316,24 @@ def main():
             "traffic": traffic, "kernel": f"k_{dom}<16,6,3>",
             "peak_source": "measured" if peaks else "fallback",
             "algorithmic_bytes_per_symiter": ALG_BYTES_PER_SYMITER[dom] * q}
-    gpu_launches = args.steps * (2 + 3)   # PUS: channel + decode; SUS: channel + init + decode
+    gpu_launches = args.steps * sum(2 if s == "pus" else 3 for s in scheds)  # channel (+ SUS init) + decode
 
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "q": q, "N": N, "M": b.code.M, "code": "regular (3,6) rate 1/2",
                        "channel": "BI-AWGN, Eb/N0 1.0/1.5/2.0 dB round-robin", "frames_per_gpu": F,
-                       "max_iter": b.max_iter, "schedules": list(scheds), "l2": "flushed between steps (256 MB write)",
+                       "max_iter": max_iter, "schedules": list(scheds), "check_method": args.method,
+                       "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"frames sharded over {world} GPU(s), no collective"},
-            "sym_iter_per_s": sum(per[s]["sym_iter_per_s"] for s in scheds) / 2,
-            "pus": per["pus"], "sus": per["sus"],
-            "sus_pus_iteration_ratio": per["sus"]["mean_iters"] / per["pus"]["mean_iters"],
-            "latency_ms": {"batch_pus": per["pus"]["kernel_ms"], "batch_sus": per["sus"]["kernel_ms"]},
+            "sym_iter_per_s": sum(per[s]["sym_iter_per_s"] for s in scheds) / len(scheds),
+            **{s: per[s] for s in scheds},
+            "sus_pus_iteration_ratio": (per["sus"]["mean_iters"] / per["pus"]["mean_iters"]
+                                        if len(scheds) == 2 else None),
+            "latency_ms": {f"batch_{s}": per[s]["kernel_ms"] for s in scheds},
             "roofline": roof, "clocks": clocks, "gpu_launches": gpu_launches, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(b, 96, b.max_iter)
+        line["cpu_baseline"] = cpu_baseline(b, 96, max_iter)
     if rank == 0:
         print(json.dumps(line), flush=True)
     code.close()

@@ -33,9 +33,10 @@ def gpu_decode(code_dev, obs, channel, param, schedule, max_iter, T=None, K=0, s
 
 
 # Relative perturbation of the channel parameter used to find each frame's
-# conditioning horizon (about ten FP32 ulps, the size of the rounding the
-# device path adds to every message).
-HORIZON_REL = 1e-6
+# conditioning horizon: the size of the largest per-iteration deviation of an
+# FP32 path from the FP64 oracle in lock-step (1e-5 .. 1e-4), so that frames
+# whose trajectory an FP32 decoder cannot follow are found before it diverges.
+HORIZON_REL = 1e-4
 
 
 def oracle_horizon(oracle, code, obs, kind, param, schedule, max_iter, gap_thr=TIE_GAP, **kw):
