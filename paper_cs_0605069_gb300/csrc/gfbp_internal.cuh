@@ -561,6 +561,8 @@ __device__ __forceinline__ void markov_prior(const DecodeArgs& A, int f, int i, 
 enum Method { kDirect = 0, kTransform = 1 };
 
 cudaError_t launch_channel(const DecodeArgs& A, cudaStream_t s);
+bool sus_team_eligible(const DecodeArgs& A);
+cudaError_t launch_sus_team(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s);
