@@ -40,20 +40,33 @@ __device__ __forceinline__ unsigned lanes_mask() {
 }
 
 // out[v] = sum_x sa[x] sb[x XOR y] for y = g*V + v (whole vectors in shared memory).
+// Four partial sums per output keep the dependent FMA chain short.
 template <int Q, int V>
 __device__ __forceinline__ void xconv_team(float (&out)[V], const float* sa, const float* sb, int g) {
+    constexpr int NP = (Q / V) < 4 ? (Q / V) : 4;
+    float acc[NP][V];
 #pragma unroll
-    for (int v = 0; v < V; v++) out[v] = 0.f;
+    for (int p = 0; p < NP; p++)
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[p][v] = 0.f;
 #pragma unroll
     for (int xb = 0; xb < Q; xb += V) {
         float a[V], b[V];
         ldv<V>(a, sa + xb);
         ldv<V>(b, sb + (xb ^ (g * V)));
+        const int p = (xb / V) % NP;
 #pragma unroll
         for (int xl = 0; xl < V; xl++) {
 #pragma unroll
-            for (int v = 0; v < V; v++) out[v] = fmaf(a[xl], b[xl ^ v], out[v]);
+            for (int v = 0; v < V; v++) acc[p][v] = fmaf(a[xl], b[xl ^ v], acc[p][v]);
         }
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        float sum = 0.f;
+#pragma unroll
+        for (int p = 0; p < NP; p++) sum += acc[p][v];
+        out[v] = sum;
     }
 }
 
@@ -99,16 +112,20 @@ __device__ __forceinline__ int slot_argmax(const float (&x)[V], unsigned smask, 
 template <int Q, int DC>
 struct SlotBuf {
     float D[DC][TeamLay<Q>::V];
-    int4 info;   // {edge, row start, row degree | h << 8, row}
-    int d;       // column degree
+    float L[TeamLay<Q>::V];  // channel likelihood of the column's symbol
+    int4 info;               // {edge, row start, row degree | h << 8, row}
+    int d;                   // column degree
+    int dep;                 // column shares a check with the previous one
 };
 
 template <int Q, int DC>
-__device__ __forceinline__ void slot_load(SlotBuf<Q, DC>& b, const DecodeArgs& A, const float* slab, int j, int k,
-                                          int g) {
+__device__ __forceinline__ void slot_load(SlotBuf<Q, DC>& b, const DecodeArgs& A, const float* slab, int f, int j,
+                                          int k, int g) {
     constexpr int V = TeamLay<Q>::V;
     const int c0 = A.c.colptr[j];
     b.d = A.c.colptr[j + 1] - c0;
+    b.dep = A.c.cdep[j];
+    ldg_v<V>(b.L, A.L + ((size_t)f * A.c.N + j) * Q + g * V);
     if (k < b.d) {
         b.info = A.c.cinfo[c0 + k];
         const int e0 = b.info.y, dc = b.info.z & 255;
@@ -148,6 +165,8 @@ __global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
     constexpr int SCR = 2 * Q + 4;   // per slot: two operand vectors (+ bank padding)
     __shared__ uint8_t s_exp[512];
     __shared__ uint8_t s_log[256];
+    __shared__ uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a
+    __shared__ uint8_t s_div[Q * Q];   // s_div[h*Q + b] = h^-1 b
     __shared__ __align__(16) float s_scr[(kTeamThreads / GS) * SCR];
 
     const int tid = threadIdx.x;
@@ -161,6 +180,12 @@ __global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
     float* sb = sa + Q;
     for (int x = tid; x < 512; x += blockDim.x) s_exp[x] = A.c.gexp[x];
     for (int x = tid; x < 256; x += blockDim.x) s_log[x] = A.c.glog[x];
+    __syncthreads();
+    for (int x = tid; x < Q * Q; x += blockDim.x) {
+        const int hh = x / Q, a = x % Q;
+        s_mul[x] = (uint8_t)gf_mul(s_exp, s_log, hh, a);
+        s_div[x] = hh ? (uint8_t)gf_div<Q>(s_exp, s_log, a, hh) : 0;
+    }
     __syncthreads();
     const int M = A.c.M, N = A.c.N;
     const long long E = A.c.E;
@@ -177,9 +202,9 @@ __global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
         int t = 1, ok = 0;
         for (;; t++) {
             SlotBuf<Q, DC> cur, nxt;
-            slot_load<Q, DC>(cur, A, slab, 0, k, g);
+            slot_load<Q, DC>(cur, A, slab, f, 0, k, g);
             for (int j = 0; j < N; j++) {
-                if (j + 1 < N) slot_load<Q, DC>(nxt, A, slab, j + 1, k, g);
+                if (j + 1 < N) slot_load<Q, DC>(nxt, A, slab, f, j + 1, k, g);
                 const int d = cur.d;
                 const bool act = k < d;
                 const int4 in = cur.info;
@@ -215,7 +240,7 @@ __global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
                 __syncwarp(smask);
                 float R[V];
 #pragma unroll
-                for (int v = 0; v < V; v++) R[v] = sa[(z ^ gf_mul(s_exp, s_log, h, g * V + v)) & (Q - 1)];
+                for (int v = 0; v < V; v++) R[v] = sa[(z ^ s_mul[h * Q + g * V + v]) & (Q - 1)];
                 __syncwarp(smask);
                 slot_normalise<Q, GS, V>(R, smask);
                 if (!act) {
@@ -224,7 +249,8 @@ __global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
                 }
                 // step 2: products over the other slots' r at the same entries
                 float p[V];
-                ldg_v<V>(p, A.L + ((size_t)f * N + j) * Q + g * V);
+#pragma unroll
+                for (int v = 0; v < V; v++) p[v] = cur.L[v];
                 if (A.markov) {
                     const int si = A.src_index[j];
                     if (si >= 0) {
@@ -263,11 +289,11 @@ __global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
                 stv<V>(sa + g * V, other);
                 __syncwarp(smask);
 #pragma unroll
-                for (int v = 0; v < V; v++) other[v] = sa[gf_div<Q>(s_exp, s_log, g * V + v, h)];
+                for (int v = 0; v < V; v++) other[v] = sa[s_div[h * Q + g * V + v]];
                 __syncwarp(smask);
                 if (act) stv<V>(slab + (size_t)in.x * Q + g * V, other);
                 if (j + 1 < N) {
-                    if (A.c.cdep[j + 1]) slot_load<Q, DC>(nxt, A, slab, j + 1, k, g);
+                    if (nxt.dep) slot_load<Q, DC>(nxt, A, slab, f, j + 1, k, g);
                     cur = nxt;
                 }
             }
@@ -276,7 +302,7 @@ __global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
             for (int i = tl; i < M; i += TEAM) {
                 int s = 0;
                 const int e1 = A.c.rowptr[i + 1];
-                for (int e = A.c.rowptr[i]; e < e1; e++) s ^= gf_mul(s_exp, s_log, A.c.eh[e], xh[A.c.ecol[e]]);
+                for (int e = A.c.rowptr[i]; e < e1; e++) s ^= s_mul[A.c.eh[e] * Q + xh[A.c.ecol[e]]];
                 bad |= (s != (zf ? (zf[i] & (Q - 1)) : 0));
             }
 #pragma unroll
