@@ -159,10 +159,10 @@ __device__ __forceinline__ void team_prior(const DecodeArgs& A, int f, int i, fl
 }
 
 template <int Q, int DC>
-__global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
+__global__ void __launch_bounds__(kTeamThreads, 6) k_sus_team(const DecodeArgs A) {
     using TL = TeamLay<Q>;
     constexpr int GS = TL::GS, V = TL::V, TEAM = TL::TEAM;
-    constexpr int SCR = 2 * Q + 4;   // per slot: two operand vectors (+ bank padding)
+    constexpr int SCR = (DC - 1 > 4 ? 2 * (DC - 1) : 8) * Q + 4;   // per slot: operands of one tree level (+ pad)
     __shared__ uint8_t s_exp[512];
     __shared__ uint8_t s_log[256];
     __shared__ uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a
@@ -177,7 +177,6 @@ __global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
     const unsigned smask = lanes_mask<GS>();
     const int team_lane0 = (threadIdx.x & 31) & ~(TEAM - 1);
     float* sa = s_scr + (tid / GS) * SCR;
-    float* sb = sa + Q;
     for (int x = tid; x < 512; x += blockDim.x) s_exp[x] = A.c.gexp[x];
     for (int x = tid; x < 256; x += blockDim.x) s_log[x] = A.c.glog[x];
     __syncthreads();
@@ -213,28 +212,39 @@ __global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
                 const int h = act ? ((in.z >> 8) & 255) : 1;
                 const int z = (act && zf) ? (zf[in.w] & (Q - 1)) : 0;
                 // step 1: distribution of the XOR-sum of the check's other edges,
-                // folded in neighbour order without divergence between slots
-                float U[V];
+                // a pairwise convolution tree over its c = dc - 1 neighbours
+                // (depth 3 for c <= 8; the convolutions of one level interleave),
+                // the same instruction stream in every slot
+                constexpr int NT = DC - 1;   // at most DC - 1 other edges
+                const int c = dc - 1;
+                float T[NT][V];
 #pragma unroll
-                for (int v = 0; v < V; v++) U[v] = (g * V + v) == 0 ? 1.f : 0.f;
+                for (int n = 0; n < NT; n++) {
 #pragma unroll
-                for (int n = 0; n < DC - 1; n++) {
-                    if (n < dc - 1) {
-                        float Y[V];
+                    for (int v = 0; v < V; v++) T[n][v] = (n >= own) ? cur.D[n + 1][v] : cur.D[n][v];
+                }
 #pragma unroll
-                        for (int v = 0; v < V; v++) Y[v] = (n >= own) ? cur.D[n + 1][v] : cur.D[n][v];
-                        if (n == 0) {
+                for (int w = 1; w < NT; w <<= 1) {          // level: pairs (n, n + w), n multiple of 2w
+                    bool any = false;
 #pragma unroll
-                            for (int v = 0; v < V; v++) U[v] = Y[v];
-                        } else {
-                            stv<V>(sa + g * V, U);
-                            stv<V>(sb + g * V, Y);
-                            __syncwarp(smask);
-                            xconv_team<Q, V>(U, sa, sb, g);
-                            __syncwarp(smask);
+                    for (int n = 0; n + w < NT; n += 2 * w) {
+                        if (n + w < c) {
+                            stv<V>(sa + (n / w) * Q + g * V, T[n]);
+                            stv<V>(sa + (n / w + 1) * Q + g * V, T[n + w]);
+                            any = true;
                         }
                     }
+                    if (any) {
+                        __syncwarp(smask);
+#pragma unroll
+                        for (int n = 0; n + w < NT; n += 2 * w)
+                            if (n + w < c) xconv_team<Q, V>(T[n], sa + (n / w) * Q, sa + (n / w + 1) * Q, g);
+                        __syncwarp(smask);
+                    }
                 }
+                float U[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) U[v] = (c > 0) ? T[0][v] : ((g * V + v) == 0 ? 1.f : 0.f);
                 // r_ij[a] = s[z XOR h a], normalised
                 stv<V>(sa + g * V, U);
                 __syncwarp(smask);
@@ -359,9 +369,9 @@ bool sus_team_eligible(const DecodeArgs& A) {
 
 cudaError_t launch_sus_team(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     switch (A.c.q) {
-    case 4: return launch_team_q<4, 8>(A, num_sms, s);
-    case 8: return launch_team_q<8, 8>(A, num_sms, s);
-    case 16: return launch_team_q<16, 8>(A, num_sms, s);
+    case 4: return A.c.dcmax <= 6 ? launch_team_q<4, 6>(A, num_sms, s) : launch_team_q<4, 8>(A, num_sms, s);
+    case 8: return A.c.dcmax <= 6 ? launch_team_q<8, 6>(A, num_sms, s) : launch_team_q<8, 8>(A, num_sms, s);
+    case 16: return A.c.dcmax <= 6 ? launch_team_q<16, 6>(A, num_sms, s) : launch_team_q<16, 8>(A, num_sms, s);
     }
     return cudaErrorInvalidValue;
 }
