@@ -1,7 +1,7 @@
 // Sequential updating scheme (SUS; Sec. 2, steps 1-4) with the
 // probability-domain check node, for q <= 16 and codes with column degree
-// <= 4 and row degree <= 8: one lane team per frame (one warp for q = 8, 16;
-// half a warp for q = 2, 4).  The team has four slots of GS lanes; slot k
+// <= 4 and row degree <= 8: one team of 16 lanes per frame (two frames per
+// warp).  The team has four slots of GS = 4 lanes; slot k
 // handles the k-th check of the current column, so step 1 (r_ij for every
 // check of column j) runs for all of the column's checks at once, and step 2
 // (q_ij, Q_j) exchanges the r_ij between slots with shuffles.
@@ -23,7 +23,7 @@ constexpr int kSlots = 4;
 
 template <int Q>
 struct TeamLay {
-    static constexpr int GS = Q < 8 ? Q : 8;       // lanes per vector
+    static constexpr int GS = 4;                     // lanes per vector
     static constexpr int V = Q / GS;                 // entries per lane
     static constexpr int TEAM = kSlots * GS;         // lanes per frame
     static_assert(TEAM == 16 || TEAM == 32 || TEAM == 8, "team must divide a warp");
@@ -159,10 +159,10 @@ __device__ __forceinline__ void team_prior(const DecodeArgs& A, int f, int i, fl
 }
 
 template <int Q, int DC>
-__global__ void __launch_bounds__(kTeamThreads, 6) k_sus_team(const DecodeArgs A) {
+__global__ void __launch_bounds__(kTeamThreads) k_sus_team(const DecodeArgs A) {
     using TL = TeamLay<Q>;
     constexpr int GS = TL::GS, V = TL::V, TEAM = TL::TEAM;
-    constexpr int SCR = (DC - 1 > 4 ? 2 * (DC - 1) : 8) * Q + 4;   // per slot: operands of one tree level (+ pad)
+    constexpr int SCR = 2 * Q + 4;   // per slot: two operand vectors (+ bank padding)
     __shared__ uint8_t s_exp[512];
     __shared__ uint8_t s_log[256];
     __shared__ uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a
@@ -212,39 +212,29 @@ __global__ void __launch_bounds__(kTeamThreads, 6) k_sus_team(const DecodeArgs A
                 const int h = act ? ((in.z >> 8) & 255) : 1;
                 const int z = (act && zf) ? (zf[in.w] & (Q - 1)) : 0;
                 // step 1: distribution of the XOR-sum of the check's other edges,
-                // a pairwise convolution tree over its c = dc - 1 neighbours
-                // (depth 3 for c <= 8; the convolutions of one level interleave),
-                // the same instruction stream in every slot
-                constexpr int NT = DC - 1;   // at most DC - 1 other edges
+                // folded in neighbour order (the same instruction stream in every slot)
                 const int c = dc - 1;
-                float T[NT][V];
-#pragma unroll
-                for (int n = 0; n < NT; n++) {
-#pragma unroll
-                    for (int v = 0; v < V; v++) T[n][v] = (n >= own) ? cur.D[n + 1][v] : cur.D[n][v];
-                }
-#pragma unroll
-                for (int w = 1; w < NT; w <<= 1) {          // level: pairs (n, n + w), n multiple of 2w
-                    bool any = false;
-#pragma unroll
-                    for (int n = 0; n + w < NT; n += 2 * w) {
-                        if (n + w < c) {
-                            stv<V>(sa + (n / w) * Q + g * V, T[n]);
-                            stv<V>(sa + (n / w + 1) * Q + g * V, T[n + w]);
-                            any = true;
-                        }
-                    }
-                    if (any) {
-                        __syncwarp(smask);
-#pragma unroll
-                        for (int n = 0; n + w < NT; n += 2 * w)
-                            if (n + w < c) xconv_team<Q, V>(T[n], sa + (n / w) * Q, sa + (n / w + 1) * Q, g);
-                        __syncwarp(smask);
-                    }
-                }
                 float U[V];
 #pragma unroll
-                for (int v = 0; v < V; v++) U[v] = (c > 0) ? T[0][v] : ((g * V + v) == 0 ? 1.f : 0.f);
+                for (int v = 0; v < V; v++) U[v] = (g * V + v) == 0 ? 1.f : 0.f;
+#pragma unroll
+                for (int n = 0; n < DC - 1; n++) {
+                    if (n < c) {
+                        float Y[V];
+#pragma unroll
+                        for (int v = 0; v < V; v++) Y[v] = (n >= own) ? cur.D[n + 1][v] : cur.D[n][v];
+                        if (n == 0) {
+#pragma unroll
+                            for (int v = 0; v < V; v++) U[v] = Y[v];
+                        } else {
+                            stv<V>(sa + g * V, U);
+                            stv<V>(sa + Q + g * V, Y);
+                            __syncwarp(smask);
+                            xconv_team<Q, V>(U, sa, sa + Q, g);
+                            __syncwarp(smask);
+                        }
+                    }
+                }
                 // r_ij[a] = s[z XOR h a], normalised
                 stv<V>(sa + g * V, U);
                 __syncwarp(smask);
