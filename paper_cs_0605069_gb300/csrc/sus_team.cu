@@ -1,7 +1,7 @@
 // Sequential updating scheme (SUS; Sec. 2, steps 1-4) with the
 // probability-domain check node, for q <= 16 and codes with column degree
-// <= 4 and row degree <= 8: one team of 16 lanes per frame (two frames per
-// warp).  The team has four slots of GS = 4 lanes; slot k
+// <= 4 and row degree <= 8: one lane team per frame (one warp for q = 8, 16;
+// half a warp for q = 4).  The team has four slots of GS lanes; slot k
 // handles the k-th check of the current column, so step 1 (r_ij for every
 // check of column j) runs for all of the column's checks at once, and step 2
 // (q_ij, Q_j) exchanges the r_ij between slots with shuffles.
@@ -23,7 +23,7 @@ constexpr int kSlots = 4;
 
 template <int Q>
 struct TeamLay {
-    static constexpr int GS = 4;                     // lanes per vector
+    static constexpr int GS = Q < 8 ? Q : 8;       // lanes per vector
     static constexpr int V = Q / GS;                 // entries per lane
     static constexpr int TEAM = kSlots * GS;         // lanes per frame
     static_assert(TEAM == 16 || TEAM == 32 || TEAM == 8, "team must divide a warp");
