@@ -165,6 +165,30 @@ gfbp_status gfbp_decode(const gfbp_code* code, int32_t n_frames, const float* ob
                         int32_t* iters, uint8_t* converged, const gfbp_options* options, void* stream);
 
 /*
+ * gfbp_decode without any device allocation.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory on
+ * their decode path: real-time receivers that fix their device footprint at
+ * start-up and forbid allocation per request (allocation time and
+ * fragmentation are unpredictable), and plug-ins into programs whose own
+ * caching allocator already holds the free device memory, where a cudaMalloc
+ * of the library could fail or fragment that pool.
+ *   Arguments, outputs and results are those of gfbp_decode.  The scratch is
+ *   a static 32 MiB device array inside the library (reserved on every device
+ *   that loads the library, until the process exits); options->workspace is
+ *   ignored.  A batch whose scratch (gfbp_workspace_size) exceeds 32 MiB is
+ *   rejected with GFBP_EINVAL before any launch; decode it in smaller calls.
+ *   The first call on a device, with that device current, looks up the
+ *   array's device address (cudaGetSymbolAddress); make that first call
+ *   before any stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU (on
+ *   different streams or host threads, without ordering between them) race
+ *   and corrupt each other's results.  No device memory is allocated or freed.
+ */
+gfbp_status gfbp_decode_noalloc(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
+                                gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter, uint8_t* x_hat,
+                                int32_t* iters, uint8_t* converged, const gfbp_options* options, void* stream);
+
+/*
  * Exactly one iteration of the schedule from a caller-supplied state, for
  * lock-step comparison with a reference.
  *   msg        device [F][E][q] in/out: q_ij before the iteration; q_ij after it.

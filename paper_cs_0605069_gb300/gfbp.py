@@ -25,7 +25,7 @@ CHECK_METHOD = {"auto": 0, "transform": 1, "direct": 2}
 
 # Functions declared in include/gfbp.h (the CPU test checks that every one is exported).
 EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info",
-           "gfbp_workspace_size", "gfbp_decode", "gfbp_step")
+           "gfbp_workspace_size", "gfbp_decode", "gfbp_step", "gfbp_decode_noalloc")
 
 
 class GfbpError(RuntimeError):
@@ -68,7 +68,9 @@ def lib() -> C.CDLL:
                                       C.POINTER(gfbp_options), P]
             L.gfbp_step.argtypes = [P, i32, P, gfbp_channel, i32, C.POINTER(gfbp_prior), P, P, P, P, P, P,
                                     C.POINTER(gfbp_options), P]
-            for fn in ("gfbp_code_create", "gfbp_code_info", "gfbp_workspace_size", "gfbp_decode", "gfbp_step"):
+            L.gfbp_decode_noalloc.argtypes = L.gfbp_decode.argtypes
+            for fn in ("gfbp_code_create", "gfbp_code_info", "gfbp_workspace_size", "gfbp_decode", "gfbp_step",
+                       "gfbp_decode_noalloc"):
                 getattr(L, fn).restype = C.c_int
             _lib = L
     return _lib
@@ -206,3 +208,28 @@ def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedul
                         _ptr(prior_out), _ptr(post), _ptr(x_hat), _ptr(sat), C.byref(opt), _stream(stream)),
         "gfbp_step")
     return dict(msg=msg, post=post, x_hat=x_hat, sat=sat, prior_out=prior_out)
+
+
+def decode_noalloc(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: str = "pus",
+                   max_iter: int = 100, T=None, K: int = 0, src_pos=None, frame_param=None, post: bool = False,
+                   check_method: str = "auto", out=None, stream=None):
+    """gfbp_decode_noalloc on CUDA tensors: like decode(), with the library's
+    static device scratch instead of a workspace (no device allocation inside
+    the library; the outputs here are caller tensors)."""
+    import torch
+    F = int(obs.shape[0])
+    dev = obs.device
+    if out is None:
+        out = dict(x_hat=torch.empty((F, code.N), dtype=torch.uint8, device=dev),
+                   iters=torch.empty(F, dtype=torch.int32, device=dev),
+                   converged=torch.empty(F, dtype=torch.uint8, device=dev))
+        if post:
+            out["post"] = torch.empty((F, code.N, code.q), dtype=torch.float32, device=dev)
+    pr, _keep = _prior(T, K, src_pos)
+    opt = gfbp_options(None, None, _ptr(out.get("post")), None, 0, None, 0)
+    opt.check_method = CHECK_METHOD[check_method]
+    ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
+    _ok(lib().gfbp_decode_noalloc(code.handle, F, _ptr(obs), ch, SCHEDULE[schedule], C.byref(pr), int(max_iter),
+                                  _ptr(out["x_hat"]), _ptr(out["iters"]), _ptr(out["converged"]), C.byref(opt),
+                                  _stream(stream)), "gfbp_decode_noalloc")
+    return out
