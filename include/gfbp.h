@@ -203,6 +203,54 @@ gfbp_status gfbp_step(const gfbp_code* code, int32_t n_frames, const float* obs,
                       float* prior_out, float* post, uint8_t* x_hat, uint8_t* sat,
                       const gfbp_options* options, void* stream);
 
+/* --------------------------------------------------------------- batching */
+/*
+ * Frames of several codes — uneven q and N — decoded by one persistent launch
+ * over a device frame table (the decoding of every frame is that of
+ * gfbp_decode, Sec. 2).  gfbp_batch_create validates the items, allocates one
+ * device block (frame table, per-item workspaces) and copies the item
+ * descriptors, synchronously; gfbp_batch_run then only enqueues kernels on
+ * `stream` (no allocation, no host synchronisation, no host-to-device copy),
+ * so a run can be captured in a CUDA graph and replayed.  Each run re-reads
+ * the items' obs and rewrites their outputs; runs of one batch must not
+ * overlap on the GPU (they share the workspaces).
+ * Limits: 1..16 items; every code with row degree <= 6 and column degree <= 3.
+ */
+typedef struct {
+    const gfbp_code* code;
+    int32_t n_frames;
+    const float* obs;          /* device, as for gfbp_decode */
+    gfbp_channel channel;
+    const gfbp_prior* prior;   /* NULL = i.i.d.; read during gfbp_batch_create only */
+    uint8_t* x_hat;            /* device [F][N] */
+    int32_t* iters;            /* device [F] */
+    uint8_t* converged;        /* device [F] */
+} gfbp_batch_item;
+
+typedef struct gfbp_batch gfbp_batch;
+
+/* options: only check_method AUTO is used; per-call options are rejected. */
+gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n_items, gfbp_schedule schedule,
+                              int32_t max_iter, const gfbp_options* options, gfbp_batch** out);
+gfbp_status gfbp_batch_run(gfbp_batch* batch, void* stream);
+/* Kernel variant chosen for every item (host [n_items]; values as in gfbp_autotune). */
+gfbp_status gfbp_batch_variants(const gfbp_batch* batch, int32_t* variants);
+void gfbp_batch_destroy(gfbp_batch* batch);
+
+/*
+ * Autotuner: time every kernel variant that computes the same arithmetic for
+ * this code and schedule (for SUS with q <= 16: one lane team per frame with a
+ * slot per check, or one lane group per frame) on the caller's sample of
+ * n_frames frames, and remember the fastest for codes of the same (q, N, M, E)
+ * and schedule on this device; later gfbp_batch_create calls use it.
+ * Synchronous; allocates its own scratch.  *chosen receives the variant:
+ * 0-2 team q = 4/8/16, 3-6 group probability route q = 2/4/8/16,
+ * 7-10 group transform route q = 32/64/128/256.
+ */
+gfbp_status gfbp_autotune(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
+                          gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter, void* stream,
+                          int32_t* chosen);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,455 @@
+// Batches of frames of several codes — uneven q and N — decoded by ONE
+// persistent launch (per schedule) over a device frame table, with no host
+// synchronisation or allocation after gfbp_batch_create, so that a run can be
+// captured in a CUDA graph and replayed.  Each item carries the kernel variant
+// that decodes its frames (team or group SUS, probability or transform check
+// node), chosen by the autotuner (gfbp_autotune) or by default rules.
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "pus_frame.cuh"
+#include "sus_group.cuh"
+#include "sus_team.cuh"
+
+namespace gfbp {
+void set_error(const std::string& msg);
+cudaError_t batch_prepare_item(DecodeArgs& A, void* ws, const gfbp_code* code, int32_t F, const float* obs,
+                               gfbp_channel ch, gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter,
+                               uint8_t* x_hat, int32_t* iters, uint8_t* conv, const gfbp_options* opt,
+                               int method, size_t* ws_bytes, cudaStream_t stream);
+cudaError_t launch_fill_prior(const DecodeArgs& A, cudaStream_t s);
+}  // namespace gfbp
+
+namespace gfbp {
+namespace {
+
+constexpr int kMaxItems = 16;
+constexpr int kMixedThreads = 128;  // SUS: 4 warps, one frame per warp
+
+// Kernel variants a batch item can use (codes with row degree <= 6 and column
+// degree <= 3; other codes are decoded by gfbp_decode).
+enum Variant : int {
+    kTeam4 = 0, kTeam8, kTeam16,                              // SUS team, probability route
+    kGroup2D, kGroup4D, kGroup8D, kGroup16D,                  // SUS group, probability route
+    kGroup32T, kGroup64T, kGroup128T, kGroup256T,             // SUS group, transform route
+    kNumVariants
+};
+
+// Shared scratch per warp (floats) for the SUS variants.
+constexpr int kWarpScratch = 3 * 256 + 4;  // the largest: group q=256 transform route, one group per warp
+
+// Out-of-line variant bodies: each keeps its own register allocation instead
+// of the union of all variants inlined into one kernel.
+template <int Q>
+__device__ __noinline__ void sus_team_call(const DecodeArgs& A, int f, const uint8_t* mul, const uint8_t* div,
+                                           float* sa) {
+    sus_team_frame<Q, 6>(A, f, mul, div, sa);
+}
+
+template <int Q, int METHOD>
+__device__ __noinline__ void sus_group_call(const DecodeArgs& A, int f, const uint8_t* ex, const uint8_t* lg,
+                                            float* sc) {
+    sus_group_frame<Q, 6, 3, METHOD>(A, f, ex, lg, sc);
+}
+
+template <int Q, int METHOD>
+__device__ __noinline__ void pus_call(const DecodeArgs& A, int f, const uint8_t* ex, const uint8_t* lg, float* sc) {
+    pus_frame<Q, 6, 3, METHOD>(A, f, ex, lg, sc);
+}
+
+__global__ void __launch_bounds__(kMixedThreads) k_sus_mixed(const DecodeArgs* __restrict__ items,
+                                                             const int* __restrict__ prefix,
+                                                             const int* __restrict__ variant, int n_items,
+                                                             int total, int* counter) {
+    __shared__ uint8_t s_exp[kMaxItems][512];
+    __shared__ uint8_t s_log[kMaxItems][256];
+    __shared__ uint8_t s_mul[kMaxItems][256];
+    __shared__ uint8_t s_div[kMaxItems][256];
+    __shared__ int s_prefix[kMaxItems + 1];
+    __shared__ int s_var[kMaxItems];
+    __shared__ __align__(16) float s_scr[(kMixedThreads / 32) * kWarpScratch];
+    const int tid = threadIdx.x;
+    for (int i = 0; i < n_items; i++) {
+        for (int x = tid; x < 512; x += blockDim.x) s_exp[i][x] = items[i].c.gexp[x];
+        for (int x = tid; x < 256; x += blockDim.x) s_log[i][x] = items[i].c.glog[x];
+    }
+    for (int i = tid; i <= n_items; i += blockDim.x) s_prefix[i] = prefix[i];
+    for (int i = tid; i < n_items; i += blockDim.x) s_var[i] = variant[i];
+    __syncthreads();
+    for (int i = 0; i < n_items; i++) {
+        const int q = items[i].c.q;
+        if (q == 4) team_tables<4>(s_exp[i], s_log[i], s_mul[i], s_div[i], tid, blockDim.x);
+        else if (q == 8) team_tables<8>(s_exp[i], s_log[i], s_mul[i], s_div[i], tid, blockDim.x);
+        else if (q == 16) team_tables<16>(s_exp[i], s_log[i], s_mul[i], s_div[i], tid, blockDim.x);
+    }
+    __syncthreads();
+    const int lane = tid & 31;
+    float* wscr = s_scr + (tid / 32) * kWarpScratch;
+    for (;;) {
+        int gidx = 0;
+        if (lane == 0) gidx = atomicAdd(counter, 1);
+        gidx = __shfl_sync(0xffffffffu, gidx, 0);
+        if (gidx >= total) break;
+        int it = 0;
+        while (it + 1 < n_items && s_prefix[it + 1] <= gidx) it++;
+        const int f = gidx - s_prefix[it];
+        const DecodeArgs& A = items[it];
+        const uint8_t* ex = s_exp[it];
+        const uint8_t* lg = s_log[it];
+        switch (s_var[it]) {
+        case kTeam4:
+            if (lane < TeamLay<4>::TEAM)
+                sus_team_call<4>(A, f, s_mul[it], s_div[it], wscr + (lane / TeamLay<4>::GS) * (2 * 4 + 4));
+            break;
+        case kTeam8:
+            sus_team_call<8>(A, f, s_mul[it], s_div[it], wscr + (lane / TeamLay<8>::GS) * (2 * 8 + 4));
+            break;
+        case kTeam16:
+            sus_team_call<16>(A, f, s_mul[it], s_div[it], wscr + (lane / TeamLay<16>::GS) * (2 * 16 + 4));
+            break;
+        case kGroup2D:
+            if (lane < Lay<2>::G) sus_group_call<2, kDirect>(A, f, ex, lg, wscr);
+            break;
+        case kGroup4D:
+            if (lane < Lay<4>::G) sus_group_call<4, kDirect>(A, f, ex, lg, wscr);
+            break;
+        case kGroup8D:
+            if (lane < Lay<8>::G) sus_group_call<8, kDirect>(A, f, ex, lg, wscr);
+            break;
+        case kGroup16D:
+            if (lane < Lay<16>::G) sus_group_call<16, kDirect>(A, f, ex, lg, wscr);
+            break;
+        case kGroup32T:
+            if (lane < Lay<32>::G) sus_group_call<32, kTransform>(A, f, ex, lg, wscr);
+            break;
+        case kGroup64T:
+            if (lane < Lay<64>::G) sus_group_call<64, kTransform>(A, f, ex, lg, wscr);
+            break;
+        case kGroup128T:
+            if (lane < Lay<128>::G) sus_group_call<128, kTransform>(A, f, ex, lg, wscr);
+            break;
+        default:
+            if (lane < Lay<256>::G) sus_group_call<256, kTransform>(A, f, ex, lg, wscr);
+            break;
+        }
+        __syncwarp();
+    }
+}
+
+// PUS: one CTA per frame, the item's q picks the routine.
+constexpr int kMixedPusScratch = 256 * (8 * 4 + 4);  // largest pus_group_scratch over the variants (q = 4)
+
+__global__ void __launch_bounds__(kPusThreads) k_pus_mixed(const DecodeArgs* __restrict__ items,
+                                                           const int* __restrict__ prefix, int n_items, int total,
+                                                           int* counter) {
+    __shared__ uint8_t s_exp[kMaxItems][512];
+    __shared__ uint8_t s_log[kMaxItems][256];
+    __shared__ int s_prefix[kMaxItems + 1];
+    __shared__ int s_frame;
+    extern __shared__ __align__(16) float s_scr[];
+    const int tid = threadIdx.x;
+    for (int i = 0; i < n_items; i++) {
+        for (int x = tid; x < 512; x += blockDim.x) s_exp[i][x] = items[i].c.gexp[x];
+        for (int x = tid; x < 256; x += blockDim.x) s_log[i][x] = items[i].c.glog[x];
+    }
+    for (int i = tid; i <= n_items; i += blockDim.x) s_prefix[i] = prefix[i];
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_frame = atomicAdd(counter, 1);
+        __syncthreads();
+        const int gidx = s_frame;
+        if (gidx >= total) break;
+        int it = 0;
+        while (it + 1 < n_items && s_prefix[it + 1] <= gidx) it++;
+        const int f = gidx - s_prefix[it];
+        const DecodeArgs& A = items[it];
+        switch (A.c.q) {
+        case 2: pus_call<2, kDirect>(A, f, s_exp[it], s_log[it], s_scr); break;
+        case 4: pus_call<4, kDirect>(A, f, s_exp[it], s_log[it], s_scr); break;
+        case 8: pus_call<8, kDirect>(A, f, s_exp[it], s_log[it], s_scr); break;
+        case 16: pus_call<16, kDirect>(A, f, s_exp[it], s_log[it], s_scr); break;
+        case 32: pus_call<32, kTransform>(A, f, s_exp[it], s_log[it], s_scr); break;
+        case 64: pus_call<64, kTransform>(A, f, s_exp[it], s_log[it], s_scr); break;
+        case 128: pus_call<128, kTransform>(A, f, s_exp[it], s_log[it], s_scr); break;
+        default: pus_call<256, kTransform>(A, f, s_exp[it], s_log[it], s_scr); break;
+        }
+    }
+}
+
+int default_variant(int q) {
+    switch (q) {
+    case 2: return kGroup2D;
+    case 4: return kTeam4;
+    case 8: return kTeam8;
+    case 16: return kTeam16;
+    case 32: return kGroup32T;
+    case 64: return kGroup64T;
+    case 128: return kGroup128T;
+    default: return kGroup256T;
+    }
+}
+
+// SUS variants the autotuner may pick from (same arithmetic route, so the
+// same results up to the order of rounding).
+std::vector<int> sus_candidates(int q) {
+    switch (q) {
+    case 4: return {kTeam4, kGroup4D};
+    case 8: return {kTeam8, kGroup8D};
+    case 16: return {kTeam16, kGroup16D};
+    default: return {default_variant(q)};
+    }
+}
+
+int num_sms() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+// autotuner cache: (device, q, N, M, E, schedule) -> variant
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, long long, int>, int> g_tune;
+
+std::tuple<int, int, int, int, long long, int> tune_key(const gfbp_code* c, int schedule) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return {dev, c->dev.q, c->dev.N, c->dev.M, c->dev.E, schedule};
+}
+
+}  // namespace
+}  // namespace gfbp
+
+struct gfbp_batch {
+    int n_items = 0;
+    int schedule = 0;
+    int total = 0;
+    std::vector<gfbp::DecodeArgs> args;
+    std::vector<int> variant;
+    void* dmem = nullptr;      // items | prefix | variants | counter | per-item workspaces
+    gfbp::DecodeArgs* d_args = nullptr;
+    int* d_prefix = nullptr;
+    int* d_variant = nullptr;
+    int* d_counter = nullptr;
+    int grid = 0;
+    size_t pus_smem = 0;
+};
+
+using namespace gfbp;
+
+extern "C" gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n_items, gfbp_schedule schedule,
+                                         int32_t max_iter, const gfbp_options* options, gfbp_batch** out) {
+    if (!out || !items || n_items < 1 || n_items > kMaxItems) {
+        set_error("gfbp_batch_create: need 1 <= n_items <= 16 items and an output handle");
+        return GFBP_EINVAL;
+    }
+    *out = nullptr;
+    if (schedule != GFBP_PUS && schedule != GFBP_SUS) { set_error("gfbp_batch_create: unknown schedule"); return GFBP_EINVAL; }
+    if (max_iter < 1) { set_error("gfbp_batch_create: max_iter must be >= 1"); return GFBP_EINVAL; }
+    if (options && (options->syndrome || options->punct || options->xhat_trace || options->post)) {
+        set_error("gfbp_batch_create: per-call options (syndrome, punct, trace, post) are per item; use gfbp_decode");
+        return GFBP_EUNSUPPORTED;
+    }
+    gfbp_batch* b = new (std::nothrow) gfbp_batch();
+    if (!b) { set_error("gfbp_batch_create: out of host memory"); return GFBP_ENOMEM; }
+    b->n_items = n_items;
+    b->schedule = schedule;
+    std::vector<size_t> ws(n_items);
+    std::vector<int> prefix(n_items + 1, 0);
+    for (int i = 0; i < n_items; i++) {
+        const gfbp_batch_item& it = items[i];
+        if (!it.code || it.n_frames < 0 || (it.n_frames > 0 && (!it.obs || !it.x_hat || !it.iters || !it.converged))) {
+            set_error("gfbp_batch_create: item " + std::to_string(i) + " has a NULL code, input or output");
+            delete b;
+            return GFBP_EINVAL;
+        }
+        if (it.code->dev.dcmax > 6 || it.code->dev.dvmax > 3) {
+            set_error("gfbp_batch_create: item " + std::to_string(i) +
+                      ": batched kernels take row degree <= 6 and column degree <= 3");
+            delete b;
+            return GFBP_EUNSUPPORTED;
+        }
+        if (it.prior && it.prior->kind != GFBP_PRIOR_IID && it.prior->kind != GFBP_PRIOR_MARKOV) {
+            set_error("gfbp_batch_create: unknown prior kind");
+            delete b;
+            return GFBP_EINVAL;
+        }
+        gfbp_status st = gfbp_workspace_size(it.code, it.n_frames, schedule, it.prior, 0, &ws[i]);
+        if (st != GFBP_OK) { delete b; return st; }
+        prefix[i + 1] = prefix[i] + it.n_frames;
+    }
+    b->total = prefix[n_items];
+    // one allocation: items | prefix | variants | counter | workspaces
+    const size_t a_args = (sizeof(DecodeArgs) * n_items + 255) & ~(size_t)255;
+    const size_t a_small = 256 * 3;
+    size_t total = a_args + a_small;
+    std::vector<size_t> ws_off(n_items);
+    for (int i = 0; i < n_items; i++) { ws_off[i] = total; total += (ws[i] + 255) & ~(size_t)255; }
+    cudaError_t e = cudaMalloc(&b->dmem, total);
+    if (e != cudaSuccess) {
+        set_error(std::string("gfbp_batch_create: ") + cudaGetErrorString(e));
+        delete b;
+        return e == cudaErrorMemoryAllocation ? GFBP_ENOMEM : GFBP_ECUDA;
+    }
+    uint8_t* base = static_cast<uint8_t*>(b->dmem);
+    b->d_args = reinterpret_cast<DecodeArgs*>(base);
+    b->d_prefix = reinterpret_cast<int*>(base + a_args);
+    b->d_variant = reinterpret_cast<int*>(base + a_args + 256);
+    b->d_counter = reinterpret_cast<int*>(base + a_args + 512);
+    b->args.resize(n_items);
+    b->variant.resize(n_items);
+    for (int i = 0; i < n_items; i++) {
+        const gfbp_batch_item& it = items[i];
+        const int q = it.code->dev.q;
+        const int method = q <= 16 ? kDirect : kTransform;
+        size_t used = 0;
+        e = batch_prepare_item(b->args[i], base + ws_off[i], it.code, it.n_frames, it.obs, it.channel, schedule,
+                               it.prior, max_iter, it.x_hat, it.iters, it.converged, nullptr, method, &used, 0);
+        if (e != cudaSuccess) {
+            cudaFree(b->dmem);
+            delete b;
+            return GFBP_EINVAL;
+        }
+        b->args[i].work = b->d_counter;
+        int v = default_variant(q);
+        if (schedule == GFBP_SUS) {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto f = g_tune.find(tune_key(it.code, schedule));
+            if (f != g_tune.end()) v = f->second;
+        }
+        b->variant[i] = v;
+    }
+    e = cudaMemcpy(b->d_args, b->args.data(), sizeof(DecodeArgs) * n_items, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * (n_items + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_variant, b->variant.data(), sizeof(int) * n_items, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_error(std::string("gfbp_batch_create: ") + cudaGetErrorString(e));
+        cudaFree(b->dmem);
+        delete b;
+        return GFBP_ECUDA;
+    }
+    // grid: every resident CTA slot (persistent kernels)
+    int occ = 1;
+    if (schedule == GFBP_SUS) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_mixed, kMixedThreads, 0);
+        const long long want = ((long long)b->total + 3) / 4;
+        const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
+        b->grid = (int)(want < cap ? want : cap);
+    } else {
+        b->pus_smem = sizeof(float) * (size_t)kMixedPusScratch;
+        cudaFuncSetAttribute(k_pus_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->pus_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus_mixed, kPusThreads, b->pus_smem);
+        const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
+        b->grid = (int)(b->total < cap ? b->total : cap);
+    }
+    *out = b;
+    return GFBP_OK;
+}
+
+extern "C" gfbp_status gfbp_batch_run(gfbp_batch* b, void* stream_v) {
+    if (!b) { set_error("gfbp_batch_run: NULL batch"); return GFBP_EINVAL; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream_v);
+    if (b->total == 0) return GFBP_OK;
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+    for (int i = 0; i < b->n_items && e == cudaSuccess; i++) {
+        const DecodeArgs& A = b->args[i];
+        if (A.F == 0) continue;
+        e = launch_channel(A, s);
+        if (e == cudaSuccess && A.markov) e = launch_fill_prior(A, s);
+        if (e == cudaSuccess && b->schedule == GFBP_SUS) e = launch_init_dev(A, s);
+    }
+    if (e == cudaSuccess && b->grid > 0) {
+        if (b->schedule == GFBP_SUS)
+            k_sus_mixed<<<b->grid, kMixedThreads, 0, s>>>(b->d_args, b->d_prefix, b->d_variant, b->n_items, b->total,
+                                                          b->d_counter);
+        else
+            k_pus_mixed<<<b->grid, kPusThreads, b->pus_smem, s>>>(b->d_args, b->d_prefix, b->n_items, b->total,
+                                                                  b->d_counter);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        set_error(std::string("gfbp_batch_run: ") + cudaGetErrorString(e));
+        return GFBP_ECUDA;
+    }
+    return GFBP_OK;
+}
+
+extern "C" gfbp_status gfbp_batch_variants(const gfbp_batch* b, int32_t* variants) {
+    if (!b || !variants) { set_error("gfbp_batch_variants: NULL argument"); return GFBP_EINVAL; }
+    for (int i = 0; i < b->n_items; i++) variants[i] = b->variant[i];
+    return GFBP_OK;
+}
+
+extern "C" void gfbp_batch_destroy(gfbp_batch* b) {
+    if (!b) return;
+    cudaFree(b->dmem);
+    delete b;
+}
+
+extern "C" gfbp_status gfbp_autotune(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
+                                     gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter, void* stream_v,
+                                     int32_t* chosen) {
+    if (!code || !obs || n_frames < 1 || !chosen) {
+        set_error("gfbp_autotune: need a code, n_frames >= 1 frames of obs and an output");
+        return GFBP_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream_v);
+    const std::vector<int> cand = schedule == GFBP_SUS ? sus_candidates(code->dev.q)
+                                                       : std::vector<int>{default_variant(code->dev.q)};
+    void* out = nullptr;
+    const size_t N = (size_t)code->dev.N;
+    cudaError_t e = cudaMalloc(&out, (size_t)n_frames * (N + 2 * sizeof(int)) + 256);
+    if (e != cudaSuccess) {
+        set_error(std::string("gfbp_autotune: ") + cudaGetErrorString(e));
+        return GFBP_ENOMEM;
+    }
+    uint8_t* x_hat = static_cast<uint8_t*>(out);
+    int32_t* iters = reinterpret_cast<int32_t*>(x_hat + (((size_t)n_frames * N + 15) & ~(size_t)15));
+    uint8_t* conv = reinterpret_cast<uint8_t*>(iters + n_frames);
+    gfbp_batch_item item{code, n_frames, obs, channel, prior, x_hat, iters, conv};
+    gfbp_batch* b = nullptr;
+    gfbp_status st = gfbp_batch_create(&item, 1, schedule, max_iter, nullptr, &b);
+    if (st != GFBP_OK) { cudaFree(out); return st; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best = cand[0];
+    for (int v : cand) {
+        b->variant[0] = v;
+        e = cudaMemcpy(b->d_variant, &v, sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && st == GFBP_OK; rep++) {   // first run warms up
+            cudaEventRecord(e0, s);
+            st = gfbp_batch_run(b, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms += t;
+        }
+        if (st != GFBP_OK) break;
+        if (ms < best_ms) { best_ms = ms; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    gfbp_batch_destroy(b);
+    cudaFree(out);
+    if (st != GFBP_OK) return st;
+    if (e != cudaSuccess) {
+        set_error(std::string("gfbp_autotune: ") + cudaGetErrorString(e));
+        return GFBP_ECUDA;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[tune_key(code, schedule)] = best;
+    }
+    *chosen = best;
+    return GFBP_OK;
+}

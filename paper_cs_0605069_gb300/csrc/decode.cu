@@ -267,13 +267,12 @@ gfbp_status check_common(const char* fn, const gfbp_code* code, int32_t F, const
     return GFBP_OK;
 }
 
-gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel ch, gfbp_schedule schedule,
-                const Common& C, int32_t max_iter, bool step, uint8_t* x_hat, int32_t* iters, uint8_t* conv,
-                float* msg_io, const float* prior_in, float* prior_out, const gfbp_options* opt, void* stream_v) {
-    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+// DecodeArgs of one call, without the workspace pointers.
+gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const float* obs, gfbp_channel ch,
+                      const Common& C, int32_t max_iter, bool step, uint8_t* x_hat, int32_t* iters, uint8_t* conv,
+                      float* msg_io, float* prior_out, const gfbp_options* opt) {
     const CodeDev& c = code->dev;
-    const Layout l = layout(c, F, C.markov, C.K, step);
-    DecodeArgs A{};
+    A = DecodeArgs{};
     A.c = c;
     A.F = F;
     A.obs = obs;
@@ -294,18 +293,57 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
     A.step = step;
     A.msg_io = msg_io;
     A.prior_out = prior_out;
-    {
-        const int m = opt ? opt->check_method : GFBP_CHECK_AUTO;
-        if (m == GFBP_CHECK_DIRECT && c.q > 16) {
-            set_error("check_method DIRECT needs q <= 16");
-            return GFBP_EUNSUPPORTED;
-        }
-        if (m < GFBP_CHECK_AUTO || m > GFBP_CHECK_DIRECT) {
-            set_error("unknown check_method");
-            return GFBP_EINVAL;
-        }
-        A.method = (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > 16)) ? kTransform : kDirect;
+    const int m = opt ? opt->check_method : GFBP_CHECK_AUTO;
+    if (m == GFBP_CHECK_DIRECT && c.q > 16) {
+        set_error("check_method DIRECT needs q <= 16");
+        return GFBP_EUNSUPPORTED;
     }
+    if (m < GFBP_CHECK_AUTO || m > GFBP_CHECK_DIRECT) {
+        set_error("unknown check_method");
+        return GFBP_EINVAL;
+    }
+    A.method = (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > 16)) ? kTransform : kDirect;
+    return GFBP_OK;
+}
+
+// Point A into the workspace; the Markov constants are copied on `stream`.
+cudaError_t place_args(DecodeArgs& A, const Layout& l, void* ws, const Common& C, bool step, const float* prior_in,
+                       cudaStream_t stream) {
+    uint8_t* base = static_cast<uint8_t*>(ws);
+    const CodeDev& c = A.c;
+    A.work = reinterpret_cast<int*>(base + l.work);
+    A.L = reinterpret_cast<float*>(base + l.L);
+    A.msg = reinterpret_cast<float*>(base + l.msg);
+    cudaError_t e = cudaSuccess;
+    if (C.markov) {
+        A.Qsrc = reinterpret_cast<float*>(base + l.Qsrc);
+        A.P = step ? const_cast<float*>(prior_in) : reinterpret_cast<float*>(base + l.P);
+        float* Mt = reinterpret_cast<float*>(base + l.Mt);
+        float* pi = reinterpret_cast<float*>(base + l.pi);
+        int* sidx = reinterpret_cast<int*>(base + l.src_index);
+        int* spos = reinterpret_cast<int*>(base + l.src_pos);
+        A.Mt = Mt;
+        A.pi = pi;
+        A.src_index = sidx;
+        A.src_pos = spos;
+        const size_t q = (size_t)c.q;
+        e = cudaMemcpyAsync(Mt, C.Mt.data(), sizeof(float) * q * q, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pi, C.pi.data(), sizeof(float) * q, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sidx, C.src_index.data(), sizeof(int) * c.N, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(spos, C.src_pos.data(), sizeof(int) * C.K, cudaMemcpyHostToDevice, stream);
+    }
+    return e;
+}
+
+gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel ch, gfbp_schedule schedule,
+                const Common& C, int32_t max_iter, bool step, uint8_t* x_hat, int32_t* iters, uint8_t* conv,
+                float* msg_io, const float* prior_in, float* prior_out, const gfbp_options* opt, void* stream_v) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    const CodeDev& c = code->dev;
+    const Layout l = layout(c, F, C.markov, C.K, step);
+    DecodeArgs A;
+    gfbp_status st = fill_args(A, code, F, obs, ch, C, max_iter, step, x_hat, iters, conv, msg_io, prior_out, opt);
+    if (st != GFBP_OK) return st;
 
     void* ws = opt ? opt->workspace : nullptr;
     bool own = false;
@@ -320,26 +358,9 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
         if (e != cudaSuccess) return cuda_fail("workspace allocation", e);
         own = true;
     }
-    uint8_t* base = static_cast<uint8_t*>(ws);
-    A.work = reinterpret_cast<int*>(base + l.work);
-    A.L = reinterpret_cast<float*>(base + l.L);
-    A.msg = reinterpret_cast<float*>(base + l.msg);
+    if (e == cudaSuccess) e = place_args(A, l, ws, C, step, prior_in, stream);
     if (C.markov) {
-        A.Qsrc = reinterpret_cast<float*>(base + l.Qsrc);
-        A.P = step ? const_cast<float*>(prior_in) : reinterpret_cast<float*>(base + l.P);
-        float* Mt = reinterpret_cast<float*>(base + l.Mt);
-        float* pi = reinterpret_cast<float*>(base + l.pi);
-        int* sidx = reinterpret_cast<int*>(base + l.src_index);
-        int* spos = reinterpret_cast<int*>(base + l.src_pos);
-        A.Mt = Mt;
-        A.pi = pi;
-        A.src_index = sidx;
-        A.src_pos = spos;
         const size_t q = (size_t)c.q;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(Mt, C.Mt.data(), sizeof(float) * q * q, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(pi, C.pi.data(), sizeof(float) * q, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(sidx, C.src_index.data(), sizeof(int) * c.N, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(spos, C.src_pos.data(), sizeof(int) * C.K, cudaMemcpyHostToDevice, stream);
         if (!step) {
             // initial block priors: the stationary distribution (reading of Sec. 2)
             std::vector<float> P0((size_t)F * C.K * q);
@@ -365,7 +386,42 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
     return GFBP_OK;
 }
 
+__global__ void k_fill_prior(float* P, const float* pi, long long n, int q) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        P[i] = pi[i % q];
+}
+
 }  // namespace
+
+// Initial block priors (the stationary distribution) of every frame, on the device.
+cudaError_t launch_fill_prior(const DecodeArgs& A, cudaStream_t s) {
+    const long long n = (long long)A.F * A.K * A.c.q;
+    if (n == 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65535LL * 8) blocks = 65535LL * 8;
+    k_fill_prior<<<(unsigned)blocks, 256, 0, s>>>(A.P, A.pi, n, A.c.q);
+    return cudaGetLastError();
+}
+
+// A batch item's DecodeArgs placed in its workspace (Markov constants copied
+// synchronously); the batch's runs launch only.
+cudaError_t batch_prepare_item(DecodeArgs& A, void* ws, const gfbp_code* code, int32_t F, const float* obs,
+                               gfbp_channel ch, gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter,
+                               uint8_t* x_hat, int32_t* iters, uint8_t* conv, const gfbp_options* opt, int method,
+                               size_t* ws_bytes, cudaStream_t stream) {
+    Common C;
+    if (check_common("gfbp_batch_create", code, F, obs, ch, schedule, prior, C) != GFBP_OK) return cudaErrorInvalidValue;
+    if (fill_args(A, code, F, obs, ch, C, max_iter, false, x_hat, iters, conv, nullptr, nullptr, opt) != GFBP_OK)
+        return cudaErrorInvalidValue;
+    A.method = method;
+    const Layout l = layout(code->dev, F, C.markov, C.K, false);
+    if (ws_bytes) *ws_bytes = l.total;
+    cudaError_t e = place_args(A, l, ws, C, false, nullptr, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) set_error(std::string("gfbp_batch_create: ") + cudaGetErrorString(e));
+    return e;
+}
+
 }  // namespace gfbp
 
 using namespace gfbp;

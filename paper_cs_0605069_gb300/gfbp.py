@@ -25,7 +25,8 @@ CHECK_METHOD = {"auto": 0, "transform": 1, "direct": 2}
 
 # Functions declared in include/gfbp.h (the CPU test checks that every one is exported).
 EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info",
-           "gfbp_workspace_size", "gfbp_decode", "gfbp_step", "gfbp_decode_noalloc")
+           "gfbp_workspace_size", "gfbp_decode", "gfbp_step", "gfbp_decode_noalloc",
+           "gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_batch_destroy", "gfbp_autotune")
 
 
 class GfbpError(RuntimeError):
@@ -233,3 +234,90 @@ def decode_noalloc(code: Code, obs, channel: str = "bsc", param: float = 0.0, sc
                                   _ptr(out["x_hat"]), _ptr(out["iters"]), _ptr(out["converged"]), C.byref(opt),
                                   _stream(stream)), "gfbp_decode_noalloc")
     return out
+
+
+class gfbp_batch_item(C.Structure):
+    _fields_ = [("code", C.c_void_p), ("n_frames", C.c_int32), ("obs", C.c_void_p), ("channel", gfbp_channel),
+                ("prior", C.c_void_p), ("x_hat", C.c_void_p), ("iters", C.c_void_p), ("converged", C.c_void_p)]
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_typed", False):
+        P, i32 = C.c_void_p, C.c_int32
+        L.gfbp_batch_create.argtypes = [C.POINTER(gfbp_batch_item), i32, i32, i32, C.POINTER(gfbp_options),
+                                        C.POINTER(C.c_void_p)]
+        L.gfbp_batch_run.argtypes = [P, P]
+        L.gfbp_batch_variants.argtypes = [P, C.POINTER(i32)]
+        L.gfbp_batch_destroy.argtypes = [P]
+        L.gfbp_batch_destroy.restype = None
+        L.gfbp_autotune.argtypes = [P, i32, P, gfbp_channel, i32, C.POINTER(gfbp_prior), i32, P, C.POINTER(i32)]
+        for fn in ("gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_autotune"):
+            getattr(L, fn).restype = C.c_int
+        L._batch_typed = True
+    return L
+
+
+class Batch:
+    """gfbp_batch: frames of several codes decoded by one persistent launch.
+    items: list of dict(code=Code, obs=tensor, channel=str, param=float,
+    frame_param=tensor|None, T=None, K=0).  Outputs are allocated here
+    (self.outputs[i] = dict(x_hat, iters, converged))."""
+
+    def __init__(self, items, schedule: str = "sus", max_iter: int = 100):
+        import torch
+        L = _batch_lib()
+        self._keep = []
+        arr = (gfbp_batch_item * len(items))()
+        self.outputs = []
+        for i, it in enumerate(items):
+            code, obs = it["code"], it["obs"]
+            F = int(obs.shape[0])
+            o = dict(x_hat=torch.empty((F, code.N), dtype=torch.uint8, device=obs.device),
+                     iters=torch.empty(F, dtype=torch.int32, device=obs.device),
+                     converged=torch.empty(F, dtype=torch.uint8, device=obs.device))
+            self.outputs.append(o)
+            pr, keep = _prior(it.get("T"), it.get("K", 0), it.get("src_pos"))
+            self._keep += [pr, keep, obs, it.get("frame_param")]
+            arr[i] = gfbp_batch_item(code.handle, F, _ptr(obs),
+                                     gfbp_channel(CHANNEL[it["channel"]], float(it.get("param", 0.0)),
+                                                  _ptr(it.get("frame_param"))),
+                                     C.cast(C.pointer(pr), C.c_void_p) if it.get("T") is not None else None,
+                                     _ptr(o["x_hat"]), _ptr(o["iters"]), _ptr(o["converged"]))
+        h = C.c_void_p()
+        _ok(L.gfbp_batch_create(arr, len(items), SCHEDULE[schedule], int(max_iter), None, C.byref(h)),
+            "gfbp_batch_create")
+        self.handle = h
+        self.n = len(items)
+
+    def run(self, stream=None):
+        _ok(_batch_lib().gfbp_batch_run(self.handle, _stream(stream)), "gfbp_batch_run")
+        return self.outputs
+
+    def variants(self):
+        v = (C.c_int32 * self.n)()
+        _ok(_batch_lib().gfbp_batch_variants(self.handle, v), "gfbp_batch_variants")
+        return list(v)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _batch_lib().gfbp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(code: Code, obs, channel: str, param: float = 0.0, schedule: str = "sus", max_iter: int = 20,
+             frame_param=None, T=None, K: int = 0, stream=None) -> int:
+    """gfbp_autotune on a sample batch; returns the chosen kernel variant."""
+    pr, _keep = _prior(T, K, None)
+    v = C.c_int32()
+    _ok(_batch_lib().gfbp_autotune(code.handle, int(obs.shape[0]), _ptr(obs),
+                                   gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param)),
+                                   SCHEDULE[schedule], C.byref(pr), int(max_iter), _stream(stream), C.byref(v)),
+        "gfbp_autotune")
+    return v.value

@@ -1,0 +1,104 @@
+"""Batched decoding (one persistent launch over frames of several codes with
+uneven q and N) against gfbp_decode of each code alone, CUDA-graph replay of a
+batch run, and the autotuner."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    return torch, gfbp, W
+
+
+def _mixed_items(torch, gfbp, W, frames=24):
+    """Codes with q in {2, 4, 16, 64, 256} and uneven N, BI-AWGN at 1.5 dB,
+    noisy all-zero or random codewords (the channel is symmetric)."""
+    items, refs = [], []
+    specs = [(4, 96, True), (16, 200, True), (64, 96, False), (256, 48, False), (2, 120, True)]
+    for k, (q, N, enc) in enumerate(specs):
+        code = W.regular_code(q, N, cfg=f"batch{q}_{N}", encodable=enc)
+        rng = np.random.default_rng(k)
+        x = W.encode(code, rng.integers(0, q, size=(frames, code.K))) if enc else np.zeros((frames, N), np.int64)
+        sig = W.ebn0_to_sigma(1.5)
+        obs = torch.from_numpy(W.biawgn(rng, x, code.p, sig)).cuda()
+        cd = gfbp.Code.from_coo(code)
+        items.append(dict(code=cd, obs=obs, channel="awgn", param=sig))
+    return items
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_batch_equals_each_code_alone(env, schedule):
+    torch, gfbp, W = env
+    items = _mixed_items(torch, gfbp, W)
+    b = gfbp.Batch(items, schedule=schedule, max_iter=40)
+    outs = b.run()
+    torch.cuda.synchronize()
+    for it, o in zip(items, outs):
+        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule=schedule, max_iter=40)
+        torch.cuda.synchronize()
+        for k in ("x_hat", "iters", "converged"):
+            assert torch.equal(ref[k], o[k]), (it["code"].q, k)
+    b.close()
+
+
+def test_batch_run_replays_in_a_cuda_graph(env):
+    torch, gfbp, W = env
+    items = _mixed_items(torch, gfbp, W, frames=16)
+    b = gfbp.Batch(items, schedule="sus", max_iter=30)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(stream=s)           # warm up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    first = [{k: v.clone() for k, v in o.items()} for o in b.outputs]
+    for o in b.outputs:
+        for v in o.values():
+            v.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run(stream=torch.cuda.current_stream())
+    for rep in range(2):
+        for o in b.outputs:
+            for v in o.values():
+                v.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for a, o in zip(first, b.outputs):
+            for k in a:
+                assert torch.equal(a[k], o[k]), k
+    b.close()
+
+
+def test_autotune_picks_a_valid_variant_and_batches_use_it(env):
+    torch, gfbp, W = env
+    b0 = W.make_batch("gf16_n1000_awgn", frames=64)
+    code = gfbp.Code.from_coo(b0.code)
+    obs = torch.from_numpy(b0.obs).cuda()
+    fp = torch.from_numpy(b0.param.astype(np.float32)).cuda()
+    v = gfbp.autotune(code, obs, "awgn", 0.0, schedule="sus", max_iter=10, frame_param=fp)
+    assert v in (2, 6)                      # team or group, both probability route for q = 16
+    b = gfbp.Batch([dict(code=code, obs=obs, channel="awgn", frame_param=fp)], schedule="sus", max_iter=30)
+    assert b.variants() == [v]
+    outs = b.run()
+    ref = gfbp.decode(code, obs, "awgn", 0.0, schedule="sus", max_iter=30, frame_param=fp)
+    torch.cuda.synchronize()
+    assert torch.equal(ref["converged"], outs[0]["converged"])
+    same = (ref["x_hat"] == outs[0]["x_hat"]).all(1) & (ref["iters"] == outs[0]["iters"])
+    assert same.float().mean().item() > 0.95   # the team and group routes round differently
+    b.close()
+
+
+def test_batch_rejects_bad_items(env):
+    torch, gfbp, W = env
+    code = W.code_from_dense(np.array([[1, 1, 1, 1, 1, 1, 1, 1]]), 4)
+    cd = gfbp.Code.from_coo(code)
+    with pytest.raises(gfbp.GfbpError) as e:
+        gfbp.Batch([dict(code=cd, obs=torch.zeros((2, 8, 2), device="cuda"), channel="bsc", param=0.1)])
+    assert e.value.status == gfbp.GFBP_EUNSUPPORTED
