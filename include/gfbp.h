@@ -214,7 +214,8 @@ gfbp_status gfbp_step(const gfbp_code* code, int32_t n_frames, const float* obs,
  * so a run can be captured in a CUDA graph and replayed.  Each run re-reads
  * the items' obs and rewrites their outputs; runs of one batch must not
  * overlap on the GPU (they share the workspaces).
- * Limits: 1..16 items; every code with row degree <= 6 and column degree <= 3.
+ * Limits: 1..65536 items; every code with row degree <= 6 and column degree <= 3;
+ * codes of one field size must share the field polynomial.
  */
 typedef struct {
     const gfbp_code* code;
@@ -250,6 +251,65 @@ void gfbp_batch_destroy(gfbp_batch* batch);
 gfbp_status gfbp_autotune(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
                           gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter, void* stream,
                           int32_t* chosen);
+
+/* ---------------------------------------------------------------- serving */
+/*
+ * Continuous batching of decode requests (each the decoding of gfbp_decode,
+ * Sec. 2).  The server reserves one device pool of hbm_budget_bytes and runs
+ * a worker thread in rounds: queued requests are admitted in arrival order
+ * while their device footprint (message workspace, inputs, outputs, state)
+ * fits in the pool's free space; one persistent launch per schedule then
+ * advances every frame of every resident request by at most round_iters
+ * iterations from where it stopped (message state stays resident between
+ * rounds); frames that stopped are retired after the round, their outputs
+ * written to the request's host buffers and their space freed.  Requests that
+ * arrive while others are on the GPU join at the next round boundary.  A
+ * frame's result does not depend on what else is resident.
+ * Codes: row degree <= 6, column degree <= 3; codes of one field size must
+ * share the field polynomial.
+ */
+typedef struct gfbp_server gfbp_server;
+
+typedef struct {
+    const gfbp_code* code;
+    int32_t n_frames;
+    const float* obs;          /* HOST [F][N][p] (or [F][N][q] log-likelihoods); copied at submit */
+    gfbp_channel channel;      /* frame_param, if set, is a HOST [F] array, copied at submit */
+    const gfbp_prior* prior;   /* NULL = i.i.d.; copied at submit */
+    gfbp_schedule schedule;
+    int32_t max_iter;
+    uint8_t* x_hat;            /* HOST [F][N], written before the request completes */
+    int32_t* iters;            /* HOST [F] */
+    uint8_t* converged;        /* HOST [F] */
+} gfbp_request;
+
+typedef struct {
+    double latency_us;         /* submit to outputs written */
+    double queue_us;           /* submit to admission */
+    int32_t rounds;            /* rounds the request was resident */
+} gfbp_result;
+
+typedef struct {
+    int32_t queued, resident, peak_resident;
+    int64_t rounds, completed;
+    size_t bytes_in_use, peak_bytes;
+} gfbp_server_stats_t;
+
+/* round_iters >= 1: iterations a resident frame advances per round. */
+gfbp_status gfbp_server_create(size_t hbm_budget_bytes, int32_t round_iters, gfbp_server** out);
+/* Queue a request (thread-safe).  GFBP_EINVAL if its footprint exceeds the
+ * whole budget; GFBP_EBUSY while the server drains.  The output buffers must
+ * stay valid until gfbp_server_wait returns for this id. */
+gfbp_status gfbp_server_submit(gfbp_server* server, const gfbp_request* request, uint64_t* id);
+/* Wait at most timeout_us for request id (GFBP_ETIMEOUT otherwise; the request
+ * stays queued or resident and can be waited for again).  On success the id is
+ * released. */
+gfbp_status gfbp_server_wait(gfbp_server* server, uint64_t id, int64_t timeout_us, gfbp_result* result);
+gfbp_status gfbp_server_stats(gfbp_server* server, gfbp_server_stats_t* stats);
+/* Refuse new requests and return once every queued and resident one is done. */
+gfbp_status gfbp_server_drain(gfbp_server* server);
+/* Finish the admitted and queued work, stop the worker and free the pool. */
+void gfbp_server_destroy(gfbp_server* server);
 
 #ifdef __cplusplus
 }

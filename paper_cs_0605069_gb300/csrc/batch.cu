@@ -28,7 +28,7 @@ cudaError_t launch_fill_prior(const DecodeArgs& A, cudaStream_t s);
 namespace gfbp {
 namespace {
 
-constexpr int kMaxItems = 16;
+constexpr int kMaxItems = 65536;
 constexpr int kMixedThreads = 128;  // SUS: 4 warps, one frame per warp
 
 // Kernel variants a batch item can use (codes with row degree <= 6 and column
@@ -62,32 +62,48 @@ __device__ __noinline__ void pus_call(const DecodeArgs& A, int f, const uint8_t*
     pus_frame<Q, 6, 3, METHOD>(A, f, ex, lg, sc);
 }
 
+// Index of the item holding global frame g (prefix sums, binary search).
+__device__ __forceinline__ int find_item(const int* __restrict__ prefix, int n_items, int g) {
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Field tables for every q = 2^p the items use (items of equal q share the
+// field polynomial): exp/log, and h a / h^-1 b for q <= 16.
+struct FieldTables {
+    uint8_t ex[8][512];
+    uint8_t lg[8][256];
+    uint8_t mul[3][256];
+    uint8_t div[3][256];
+};
+
+__device__ void load_fields(FieldTables& T, const DecodeArgs* items, const int* field_item, int tid, int nt) {
+    for (int p = 0; p < 8; p++) {
+        const int i = field_item[p];
+        if (i < 0) continue;
+        for (int x = tid; x < 512; x += nt) T.ex[p][x] = items[i].c.gexp[x];
+        for (int x = tid; x < 256; x += nt) T.lg[p][x] = items[i].c.glog[x];
+    }
+    __syncthreads();
+    if (field_item[1] >= 0) team_tables<4>(T.ex[1], T.lg[1], T.mul[0], T.div[0], tid, nt);
+    if (field_item[2] >= 0) team_tables<8>(T.ex[2], T.lg[2], T.mul[1], T.div[1], tid, nt);
+    if (field_item[3] >= 0) team_tables<16>(T.ex[3], T.lg[3], T.mul[2], T.div[2], tid, nt);
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kMixedThreads) k_sus_mixed(const DecodeArgs* __restrict__ items,
                                                              const int* __restrict__ prefix,
                                                              const int* __restrict__ variant, int n_items,
-                                                             int total, int* counter) {
-    __shared__ uint8_t s_exp[kMaxItems][512];
-    __shared__ uint8_t s_log[kMaxItems][256];
-    __shared__ uint8_t s_mul[kMaxItems][256];
-    __shared__ uint8_t s_div[kMaxItems][256];
-    __shared__ int s_prefix[kMaxItems + 1];
-    __shared__ int s_var[kMaxItems];
+                                                             int total, int* counter, const int* field_item) {
+    __shared__ FieldTables T;
     __shared__ __align__(16) float s_scr[(kMixedThreads / 32) * kWarpScratch];
     const int tid = threadIdx.x;
-    for (int i = 0; i < n_items; i++) {
-        for (int x = tid; x < 512; x += blockDim.x) s_exp[i][x] = items[i].c.gexp[x];
-        for (int x = tid; x < 256; x += blockDim.x) s_log[i][x] = items[i].c.glog[x];
-    }
-    for (int i = tid; i <= n_items; i += blockDim.x) s_prefix[i] = prefix[i];
-    for (int i = tid; i < n_items; i += blockDim.x) s_var[i] = variant[i];
-    __syncthreads();
-    for (int i = 0; i < n_items; i++) {
-        const int q = items[i].c.q;
-        if (q == 4) team_tables<4>(s_exp[i], s_log[i], s_mul[i], s_div[i], tid, blockDim.x);
-        else if (q == 8) team_tables<8>(s_exp[i], s_log[i], s_mul[i], s_div[i], tid, blockDim.x);
-        else if (q == 16) team_tables<16>(s_exp[i], s_log[i], s_mul[i], s_div[i], tid, blockDim.x);
-    }
-    __syncthreads();
+    load_fields(T, items, field_item, tid, blockDim.x);
     const int lane = tid & 31;
     float* wscr = s_scr + (tid / 32) * kWarpScratch;
     for (;;) {
@@ -95,22 +111,24 @@ __global__ void __launch_bounds__(kMixedThreads) k_sus_mixed(const DecodeArgs* _
         if (lane == 0) gidx = atomicAdd(counter, 1);
         gidx = __shfl_sync(0xffffffffu, gidx, 0);
         if (gidx >= total) break;
-        int it = 0;
-        while (it + 1 < n_items && s_prefix[it + 1] <= gidx) it++;
-        const int f = gidx - s_prefix[it];
+        const int it = find_item(prefix, n_items, gidx);
+        const int f = gidx - __ldg(prefix + it);
         const DecodeArgs& A = items[it];
-        const uint8_t* ex = s_exp[it];
-        const uint8_t* lg = s_log[it];
-        switch (s_var[it]) {
+        const int pf = A.c.p - 1;
+        const uint8_t* ex = T.ex[pf];
+        const uint8_t* lg = T.lg[pf];
+        const uint8_t* s_mul_it = T.mul[pf >= 1 && pf <= 3 ? pf - 1 : 0];
+        const uint8_t* s_div_it = T.div[pf >= 1 && pf <= 3 ? pf - 1 : 0];
+        switch (__ldg(variant + it)) {
         case kTeam4:
             if (lane < TeamLay<4>::TEAM)
-                sus_team_call<4>(A, f, s_mul[it], s_div[it], wscr + (lane / TeamLay<4>::GS) * (2 * 4 + 4));
+                sus_team_call<4>(A, f, s_mul_it, s_div_it, wscr + (lane / TeamLay<4>::GS) * (2 * 4 + 4));
             break;
         case kTeam8:
-            sus_team_call<8>(A, f, s_mul[it], s_div[it], wscr + (lane / TeamLay<8>::GS) * (2 * 8 + 4));
+            sus_team_call<8>(A, f, s_mul_it, s_div_it, wscr + (lane / TeamLay<8>::GS) * (2 * 8 + 4));
             break;
         case kTeam16:
-            sus_team_call<16>(A, f, s_mul[it], s_div[it], wscr + (lane / TeamLay<16>::GS) * (2 * 16 + 4));
+            sus_team_call<16>(A, f, s_mul_it, s_div_it, wscr + (lane / TeamLay<16>::GS) * (2 * 16 + 4));
             break;
         case kGroup2D:
             if (lane < Lay<2>::G) sus_group_call<2, kDirect>(A, f, ex, lg, wscr);
@@ -146,37 +164,32 @@ constexpr int kMixedPusScratch = 256 * (8 * 4 + 4);  // largest pus_group_scratc
 
 __global__ void __launch_bounds__(kPusThreads) k_pus_mixed(const DecodeArgs* __restrict__ items,
                                                            const int* __restrict__ prefix, int n_items, int total,
-                                                           int* counter) {
-    __shared__ uint8_t s_exp[kMaxItems][512];
-    __shared__ uint8_t s_log[kMaxItems][256];
-    __shared__ int s_prefix[kMaxItems + 1];
+                                                           int* counter, const int* field_item) {
+    __shared__ FieldTables T;
     __shared__ int s_frame;
     extern __shared__ __align__(16) float s_scr[];
     const int tid = threadIdx.x;
-    for (int i = 0; i < n_items; i++) {
-        for (int x = tid; x < 512; x += blockDim.x) s_exp[i][x] = items[i].c.gexp[x];
-        for (int x = tid; x < 256; x += blockDim.x) s_log[i][x] = items[i].c.glog[x];
-    }
-    for (int i = tid; i <= n_items; i += blockDim.x) s_prefix[i] = prefix[i];
+    load_fields(T, items, field_item, tid, blockDim.x);
     for (;;) {
         __syncthreads();
         if (tid == 0) s_frame = atomicAdd(counter, 1);
         __syncthreads();
         const int gidx = s_frame;
         if (gidx >= total) break;
-        int it = 0;
-        while (it + 1 < n_items && s_prefix[it + 1] <= gidx) it++;
-        const int f = gidx - s_prefix[it];
+        const int it = find_item(prefix, n_items, gidx);
+        const int f = gidx - __ldg(prefix + it);
         const DecodeArgs& A = items[it];
+        const uint8_t* ex = T.ex[A.c.p - 1];
+        const uint8_t* lg = T.lg[A.c.p - 1];
         switch (A.c.q) {
-        case 2: pus_call<2, kDirect>(A, f, s_exp[it], s_log[it], s_scr); break;
-        case 4: pus_call<4, kDirect>(A, f, s_exp[it], s_log[it], s_scr); break;
-        case 8: pus_call<8, kDirect>(A, f, s_exp[it], s_log[it], s_scr); break;
-        case 16: pus_call<16, kDirect>(A, f, s_exp[it], s_log[it], s_scr); break;
-        case 32: pus_call<32, kTransform>(A, f, s_exp[it], s_log[it], s_scr); break;
-        case 64: pus_call<64, kTransform>(A, f, s_exp[it], s_log[it], s_scr); break;
-        case 128: pus_call<128, kTransform>(A, f, s_exp[it], s_log[it], s_scr); break;
-        default: pus_call<256, kTransform>(A, f, s_exp[it], s_log[it], s_scr); break;
+        case 2: pus_call<2, kDirect>(A, f, ex, lg, s_scr); break;
+        case 4: pus_call<4, kDirect>(A, f, ex, lg, s_scr); break;
+        case 8: pus_call<8, kDirect>(A, f, ex, lg, s_scr); break;
+        case 16: pus_call<16, kDirect>(A, f, ex, lg, s_scr); break;
+        case 32: pus_call<32, kTransform>(A, f, ex, lg, s_scr); break;
+        case 64: pus_call<64, kTransform>(A, f, ex, lg, s_scr); break;
+        case 128: pus_call<128, kTransform>(A, f, ex, lg, s_scr); break;
+        default: pus_call<256, kTransform>(A, f, ex, lg, s_scr); break;
         }
     }
 }
@@ -225,19 +238,72 @@ std::tuple<int, int, int, int, long long, int> tune_key(const gfbp_code* c, int 
 }  // namespace
 }  // namespace gfbp
 
+namespace gfbp {
+
+// Field-table owner per p (item index of the first item with q = 2^p), or an
+// error when two codes of one q use different polynomials.
+bool field_owners(const std::vector<const gfbp_code*>& codes, int* owner, std::string* why) {
+    uint32_t poly[8] = {0};
+    for (int p = 0; p < 8; p++) owner[p] = -1;
+    for (size_t i = 0; i < codes.size(); i++) {
+        const int pf = codes[i]->dev.p - 1;
+        if (owner[pf] < 0) {
+            owner[pf] = (int)i;
+            poly[pf] = codes[i]->poly;
+        } else if (poly[pf] != codes[i]->poly) {
+            *why = "codes of the same field size must use the same field polynomial";
+            return false;
+        }
+    }
+    return true;
+}
+
+void mixed_shape(MixedLaunch& m) {
+    int occ = 1;
+    if (m.schedule == GFBP_SUS) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_mixed, kMixedThreads, 0);
+        const long long want = ((long long)m.total + 3) / 4;
+        const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
+        m.grid = (int)(want < cap ? want : cap);
+    } else {
+        m.pus_smem = sizeof(float) * (size_t)kMixedPusScratch;
+        cudaFuncSetAttribute(k_pus_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.pus_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus_mixed, kPusThreads, m.pus_smem);
+        const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
+        m.grid = (int)(m.total < cap ? m.total : cap);
+    }
+}
+
+cudaError_t mixed_launch(const MixedLaunch& m, cudaStream_t s) {
+    if (m.total == 0 || m.grid == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(m.d_counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if (m.schedule == GFBP_SUS)
+        k_sus_mixed<<<m.grid, kMixedThreads, 0, s>>>(m.d_args, m.d_prefix, m.d_variant, m.n_items, m.total,
+                                                     m.d_counter, m.d_field);
+    else
+        k_pus_mixed<<<m.grid, kPusThreads, m.pus_smem, s>>>(m.d_args, m.d_prefix, m.n_items, m.total, m.d_counter,
+                                                            m.d_field);
+    return cudaGetLastError();
+}
+
+int tuned_variant(const gfbp_code* code, int schedule) {
+    int v = default_variant(code->dev.q);
+    if (schedule == GFBP_SUS) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto f = g_tune.find(tune_key(code, schedule));
+        if (f != g_tune.end()) v = f->second;
+    }
+    return v;
+}
+
+}  // namespace gfbp
+
 struct gfbp_batch {
-    int n_items = 0;
-    int schedule = 0;
-    int total = 0;
     std::vector<gfbp::DecodeArgs> args;
     std::vector<int> variant;
-    void* dmem = nullptr;      // items | prefix | variants | counter | per-item workspaces
-    gfbp::DecodeArgs* d_args = nullptr;
-    int* d_prefix = nullptr;
-    int* d_variant = nullptr;
-    int* d_counter = nullptr;
-    int grid = 0;
-    size_t pus_smem = 0;
+    void* dmem = nullptr;  // items | prefix | variants | counter | field owners | per-item workspaces
+    gfbp::MixedLaunch m;
 };
 
 using namespace gfbp;
@@ -245,49 +311,46 @@ using namespace gfbp;
 extern "C" gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n_items, gfbp_schedule schedule,
                                          int32_t max_iter, const gfbp_options* options, gfbp_batch** out) {
     if (!out || !items || n_items < 1 || n_items > kMaxItems) {
-        set_error("gfbp_batch_create: need 1 <= n_items <= 16 items and an output handle");
+        set_error("gfbp_batch_create: need 1 <= n_items <= 65536 items and an output handle");
         return GFBP_EINVAL;
     }
     *out = nullptr;
     if (schedule != GFBP_PUS && schedule != GFBP_SUS) { set_error("gfbp_batch_create: unknown schedule"); return GFBP_EINVAL; }
     if (max_iter < 1) { set_error("gfbp_batch_create: max_iter must be >= 1"); return GFBP_EINVAL; }
     if (options && (options->syndrome || options->punct || options->xhat_trace || options->post)) {
-        set_error("gfbp_batch_create: per-call options (syndrome, punct, trace, post) are per item; use gfbp_decode");
+        set_error("gfbp_batch_create: per-call options (syndrome, punct, trace, post) are not taken by batches");
         return GFBP_EUNSUPPORTED;
     }
-    gfbp_batch* b = new (std::nothrow) gfbp_batch();
-    if (!b) { set_error("gfbp_batch_create: out of host memory"); return GFBP_ENOMEM; }
-    b->n_items = n_items;
-    b->schedule = schedule;
     std::vector<size_t> ws(n_items);
     std::vector<int> prefix(n_items + 1, 0);
+    std::vector<const gfbp_code*> codes(n_items);
     for (int i = 0; i < n_items; i++) {
         const gfbp_batch_item& it = items[i];
         if (!it.code || it.n_frames < 0 || (it.n_frames > 0 && (!it.obs || !it.x_hat || !it.iters || !it.converged))) {
             set_error("gfbp_batch_create: item " + std::to_string(i) + " has a NULL code, input or output");
-            delete b;
             return GFBP_EINVAL;
         }
         if (it.code->dev.dcmax > 6 || it.code->dev.dvmax > 3) {
             set_error("gfbp_batch_create: item " + std::to_string(i) +
                       ": batched kernels take row degree <= 6 and column degree <= 3");
-            delete b;
             return GFBP_EUNSUPPORTED;
         }
-        if (it.prior && it.prior->kind != GFBP_PRIOR_IID && it.prior->kind != GFBP_PRIOR_MARKOV) {
-            set_error("gfbp_batch_create: unknown prior kind");
-            delete b;
-            return GFBP_EINVAL;
-        }
         gfbp_status st = gfbp_workspace_size(it.code, it.n_frames, schedule, it.prior, 0, &ws[i]);
-        if (st != GFBP_OK) { delete b; return st; }
+        if (st != GFBP_OK) return st;
         prefix[i + 1] = prefix[i] + it.n_frames;
+        codes[i] = it.code;
     }
-    b->total = prefix[n_items];
-    // one allocation: items | prefix | variants | counter | workspaces
+    int owner[8];
+    std::string why;
+    if (!field_owners(codes, owner, &why)) {
+        set_error("gfbp_batch_create: " + why);
+        return GFBP_EUNSUPPORTED;
+    }
+    gfbp_batch* b = new (std::nothrow) gfbp_batch();
+    if (!b) { set_error("gfbp_batch_create: out of host memory"); return GFBP_ENOMEM; }
     const size_t a_args = (sizeof(DecodeArgs) * n_items + 255) & ~(size_t)255;
-    const size_t a_small = 256 * 3;
-    size_t total = a_args + a_small;
+    const size_t a_int = (sizeof(int) * (n_items + 1) + 255) & ~(size_t)255;
+    size_t total = a_args + 2 * a_int + 512;
     std::vector<size_t> ws_off(n_items);
     for (int i = 0; i < n_items; i++) { ws_off[i] = total; total += (ws[i] + 255) & ~(size_t)255; }
     cudaError_t e = cudaMalloc(&b->dmem, total);
@@ -297,56 +360,41 @@ extern "C" gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n
         return e == cudaErrorMemoryAllocation ? GFBP_ENOMEM : GFBP_ECUDA;
     }
     uint8_t* base = static_cast<uint8_t*>(b->dmem);
-    b->d_args = reinterpret_cast<DecodeArgs*>(base);
-    b->d_prefix = reinterpret_cast<int*>(base + a_args);
-    b->d_variant = reinterpret_cast<int*>(base + a_args + 256);
-    b->d_counter = reinterpret_cast<int*>(base + a_args + 512);
+    MixedLaunch& m = b->m;
+    m.d_args = reinterpret_cast<DecodeArgs*>(base);
+    m.d_prefix = reinterpret_cast<int*>(base + a_args);
+    m.d_variant = reinterpret_cast<int*>(base + a_args + a_int);
+    m.d_counter = reinterpret_cast<int*>(base + a_args + 2 * a_int);
+    m.d_field = reinterpret_cast<int*>(base + a_args + 2 * a_int + 256);
+    m.n_items = n_items;
+    m.total = prefix[n_items];
+    m.schedule = schedule;
     b->args.resize(n_items);
     b->variant.resize(n_items);
     for (int i = 0; i < n_items; i++) {
         const gfbp_batch_item& it = items[i];
         const int q = it.code->dev.q;
         const int method = q <= 16 ? kDirect : kTransform;
-        size_t used = 0;
         e = batch_prepare_item(b->args[i], base + ws_off[i], it.code, it.n_frames, it.obs, it.channel, schedule,
-                               it.prior, max_iter, it.x_hat, it.iters, it.converged, nullptr, method, &used, 0);
+                               it.prior, max_iter, it.x_hat, it.iters, it.converged, nullptr, method, nullptr, 0);
         if (e != cudaSuccess) {
             cudaFree(b->dmem);
             delete b;
             return GFBP_EINVAL;
         }
-        b->args[i].work = b->d_counter;
-        int v = default_variant(q);
-        if (schedule == GFBP_SUS) {
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            auto f = g_tune.find(tune_key(it.code, schedule));
-            if (f != g_tune.end()) v = f->second;
-        }
-        b->variant[i] = v;
+        b->variant[i] = tuned_variant(it.code, schedule);
     }
-    e = cudaMemcpy(b->d_args, b->args.data(), sizeof(DecodeArgs) * n_items, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * (n_items + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_variant, b->variant.data(), sizeof(int) * n_items, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(m.d_args, b->args.data(), sizeof(DecodeArgs) * n_items, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m.d_prefix, prefix.data(), sizeof(int) * (n_items + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m.d_variant, b->variant.data(), sizeof(int) * n_items, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m.d_field, owner, sizeof(owner), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         set_error(std::string("gfbp_batch_create: ") + cudaGetErrorString(e));
         cudaFree(b->dmem);
         delete b;
         return GFBP_ECUDA;
     }
-    // grid: every resident CTA slot (persistent kernels)
-    int occ = 1;
-    if (schedule == GFBP_SUS) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_mixed, kMixedThreads, 0);
-        const long long want = ((long long)b->total + 3) / 4;
-        const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
-        b->grid = (int)(want < cap ? want : cap);
-    } else {
-        b->pus_smem = sizeof(float) * (size_t)kMixedPusScratch;
-        cudaFuncSetAttribute(k_pus_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->pus_smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus_mixed, kPusThreads, b->pus_smem);
-        const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
-        b->grid = (int)(b->total < cap ? b->total : cap);
-    }
+    mixed_shape(m);
     *out = b;
     return GFBP_OK;
 }
@@ -354,24 +402,15 @@ extern "C" gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n
 extern "C" gfbp_status gfbp_batch_run(gfbp_batch* b, void* stream_v) {
     if (!b) { set_error("gfbp_batch_run: NULL batch"); return GFBP_EINVAL; }
     cudaStream_t s = static_cast<cudaStream_t>(stream_v);
-    if (b->total == 0) return GFBP_OK;
-    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
-    for (int i = 0; i < b->n_items && e == cudaSuccess; i++) {
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < b->args.size() && e == cudaSuccess; i++) {
         const DecodeArgs& A = b->args[i];
         if (A.F == 0) continue;
         e = launch_channel(A, s);
         if (e == cudaSuccess && A.markov) e = launch_fill_prior(A, s);
-        if (e == cudaSuccess && b->schedule == GFBP_SUS) e = launch_init_dev(A, s);
+        if (e == cudaSuccess && b->m.schedule == GFBP_SUS) e = launch_init_dev(A, s);
     }
-    if (e == cudaSuccess && b->grid > 0) {
-        if (b->schedule == GFBP_SUS)
-            k_sus_mixed<<<b->grid, kMixedThreads, 0, s>>>(b->d_args, b->d_prefix, b->d_variant, b->n_items, b->total,
-                                                          b->d_counter);
-        else
-            k_pus_mixed<<<b->grid, kPusThreads, b->pus_smem, s>>>(b->d_args, b->d_prefix, b->n_items, b->total,
-                                                                  b->d_counter);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = mixed_launch(b->m, s);
     if (e != cudaSuccess) {
         set_error(std::string("gfbp_batch_run: ") + cudaGetErrorString(e));
         return GFBP_ECUDA;
@@ -381,7 +420,7 @@ extern "C" gfbp_status gfbp_batch_run(gfbp_batch* b, void* stream_v) {
 
 extern "C" gfbp_status gfbp_batch_variants(const gfbp_batch* b, int32_t* variants) {
     if (!b || !variants) { set_error("gfbp_batch_variants: NULL argument"); return GFBP_EINVAL; }
-    for (int i = 0; i < b->n_items; i++) variants[i] = b->variant[i];
+    for (size_t i = 0; i < b->variant.size(); i++) variants[i] = b->variant[i];
     return GFBP_OK;
 }
 
@@ -422,7 +461,7 @@ extern "C" gfbp_status gfbp_autotune(const gfbp_code* code, int32_t n_frames, co
     int best = cand[0];
     for (int v : cand) {
         b->variant[0] = v;
-        e = cudaMemcpy(b->d_variant, &v, sizeof(int), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(b->m.d_variant, &v, sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) break;
         float ms = 0.f;
         for (int rep = 0; rep < 3 && st == GFBP_OK; rep++) {   // first run warms up

@@ -78,6 +78,10 @@ struct DecodeArgs {
     float* msg_io;         // [F][E][q] q_ij in (before) and out (after)
     float* prior_out;      // [F][K][q]
     int method;            // Method
+    // resumable decoding (serving): per frame the iterations done so far, with
+    // bit 30 set once the frame has stopped; NULL = whole decode in one launch
+    int* fstate;
+    int round_iters;       // resumable decoding: iterations per launch
 };
 
 // ---------------------------------------------------------------- helpers
@@ -566,6 +570,32 @@ cudaError_t launch_sus_team(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s);
+cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
+
+// One persistent launch over the frames of several items (batch.cu): device
+// arrays (items, prefix sums of their frame counts, kernel variants, frame
+// counter, field-table owner per q) and the launch shape.
+struct MixedLaunch {
+    DecodeArgs* d_args = nullptr;
+    int* d_prefix = nullptr;
+    int* d_variant = nullptr;
+    int* d_counter = nullptr;
+    int* d_field = nullptr;
+    int n_items = 0;
+    int total = 0;
+    int schedule = 0;
+    int grid = 0;
+    size_t pus_smem = 0;
+};
+
+void mixed_shape(MixedLaunch& m);
+cudaError_t mixed_launch(const MixedLaunch& m, cudaStream_t s);
+int tuned_variant(const gfbp_code* code, int schedule);
+cudaError_t launch_fill_prior(const DecodeArgs& A, cudaStream_t s);
+cudaError_t batch_prepare_item(DecodeArgs& A, void* ws, const gfbp_code* code, int32_t F, const float* obs,
+                               gfbp_channel ch, gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter,
+                               uint8_t* x_hat, int32_t* iters, uint8_t* conv, const gfbp_options* opt, int method,
+                               size_t* ws_bytes, cudaStream_t stream);
 
 }  // namespace gfbp
 

@@ -226,8 +226,14 @@ __device__ __forceinline__ void pus_frame(const DecodeArgs& A, int f, const uint
     const long long E = A.c.E;
     float* slab = A.msg + (size_t)f * E * Q;
 
+    int t0 = 0;   // iterations already done (resumable decoding)
+    if (A.fstate) {
+        const int st = A.fstate[f];
+        if (st >> 30) return;
+        t0 = st;
+    }
     // q_ij <- p_j (Sec. 2) or the caller's state, in stored form
-    for (long long e = grp; e < E; e += ngrp) {
+    for (long long e = grp; e < E && t0 == 0; e += ngrp) {
         float x[V];
         if (A.step) {
             ldv<V>(x, A.msg_io + ((size_t)f * E + e) * Q + g * V);
@@ -240,7 +246,8 @@ __device__ __forceinline__ void pus_frame(const DecodeArgs& A, int f, const uint
     }
     __syncthreads();
 
-    int t = 1, ok = 0;
+    int t = t0 + 1, ok = 0;
+    bool fin = false;
     for (;; t++) {
         for (int i = grp; i < M; i += ngrp) {
             if constexpr (METHOD == kDirect) pus_check_direct<Q, DC>(A, slab, f, i, sc, mask, g, s_exp, s_log);
@@ -262,12 +269,16 @@ __device__ __forceinline__ void pus_frame(const DecodeArgs& A, int f, const uint
             uint8_t* tr = A.trace + ((size_t)f * A.max_iter + (t - 1)) * N;
             for (int j = tid; j < N; j += blockDim.x) tr[j] = A.xhat[(size_t)f * N + j];
         }
-        if ((ok && A.early_stop) || t >= A.max_iter) break;
+        if ((ok && A.early_stop) || t >= A.max_iter) {
+            fin = true;
+            break;
+        }
         if (A.markov) {
             for (int i = grp; i < A.K; i += ngrp)
                 markov_prior<Q>(A, f, i, A.P + ((size_t)f * A.K + i) * Q, mask, g);
             __syncthreads();
         }
+        if (A.fstate && t - t0 >= A.round_iters) break;
     }
     if (A.step && A.markov && A.prior_out) {
         for (int i = grp; i < A.K; i += ngrp)
@@ -278,8 +289,11 @@ __device__ __forceinline__ void pus_frame(const DecodeArgs& A, int f, const uint
             A.trace[(size_t)f * A.max_iter * N + o] = 255;
     }
     if (tid == 0) {
-        if (A.iters) A.iters[f] = t;
-        A.conv[f] = (uint8_t)ok;
+        if (!A.fstate || fin) {
+            if (A.iters) A.iters[f] = t;
+            A.conv[f] = (uint8_t)ok;
+        }
+        if (A.fstate) A.fstate[f] = fin ? (t | (1 << 30)) : t;
     }
 }
 

@@ -1,0 +1,467 @@
+// Serving: continuous batching of decode requests on one GPU.
+//
+// A request is F frames of one code (any q, N, channel, prior, schedule).
+// The server owns one device pool of a fixed HBM budget.  A worker thread
+// runs rounds: it admits queued requests (in arrival order) whose footprint —
+// message workspace, observations, outputs and state — fits in the pool's
+// free space, sets up their state on the device, and then launches one
+// persistent kernel per schedule over the frames of every resident request,
+// each frame advancing by at most `round_iters` iterations from where it
+// stopped (its messages stay resident between rounds).  Frames that stop
+// (H x = z or max_iter, Sec. 2) are retired after the round: their outputs
+// are copied to the caller's host buffers, their pool space is freed and
+// their waiters are woken.  Requests that arrive while others run are
+// admitted at the next round boundary and share its launches.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gfbp_internal.cuh"
+
+namespace gfbp {
+void set_error(const std::string& msg);
+}
+
+using namespace gfbp;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// First-fit allocator over [0, size) of the pool (host bookkeeping only).
+class PoolAlloc {
+  public:
+    explicit PoolAlloc(size_t size) { free_[0] = size; }
+    bool alloc(size_t n, size_t* off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const size_t rest = it->second - n, start = it->first + n;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used_ += n;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        used_ -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0;
+};
+
+struct Req {
+    uint64_t id = 0;
+    const gfbp_code* code = nullptr;
+    int F = 0, schedule = 0, max_iter = 0, obs_stride = 0;
+    std::vector<float> obs, fparam;
+    gfbp_channel ch{};
+    bool markov = false;
+    std::vector<double> T;
+    std::vector<int32_t> src_pos;
+    int K = 0;
+    uint8_t* hx = nullptr;
+    int32_t* hit = nullptr;
+    uint8_t* hconv = nullptr;
+    // device placement
+    size_t off = 0, bytes = 0, ws_bytes = 0;
+    size_t o_obs = 0, o_fp = 0, o_state = 0, o_x = 0, o_it = 0, o_cv = 0, o_ws = 0;
+    DecodeArgs A{};
+    int state = 0;  // 0 queued, 1 resident, 2 done, 3 failed
+    gfbp_status status = GFBP_OK;
+    int rounds = 0;
+    Clock::time_point t_submit, t_admit, t_done;
+};
+
+struct LaunchBufs {  // device tables of one round's mixed launch
+    void* dmem = nullptr;
+    int cap = 0;
+    MixedLaunch m;
+};
+
+}  // namespace
+
+struct gfbp_server {
+    size_t budget = 0;
+    int round_iters = 8;
+    void* pool = nullptr;
+    cudaStream_t stream = nullptr;
+    std::unique_ptr<PoolAlloc> alloc;
+    LaunchBufs bufs[2];
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req*> queue;
+    std::vector<Req*> resident;
+    std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
+    uint64_t next_id = 1;
+    bool stop = false, draining = false;
+    std::thread worker;
+    int device = 0;
+    // statistics
+    long long rounds = 0, completed = 0;
+    int peak_resident = 0;
+    size_t peak_bytes = 0;
+    uint32_t field_poly[8] = {0};
+};
+
+namespace {
+
+size_t footprint(const Req& r, size_t* ws_out) {
+    size_t ws = 0;
+    gfbp_prior pr{};
+    if (r.markov) { pr.kind = GFBP_PRIOR_MARKOV; pr.T = r.T.data(); pr.K = r.K; pr.src_pos = r.src_pos.data(); }
+    gfbp_workspace_size(r.code, r.F, (gfbp_schedule)r.schedule, r.markov ? &pr : nullptr, 0, &ws);
+    *ws_out = ws;
+    const size_t N = (size_t)r.code->dev.N;
+    return a256(ws) + a256(r.obs.size() * 4) + a256(r.fparam.size() * 4) + a256((size_t)r.F * 4) +
+           a256((size_t)r.F * N) + a256((size_t)r.F * 4) + a256((size_t)r.F);
+}
+
+// Put an admitted request on the device: inputs, state, channel likelihoods
+// and initial messages.  Runs on the worker thread, on the server stream.
+gfbp_status setup(gfbp_server* S, Req& r) {
+    uint8_t* base = static_cast<uint8_t*>(S->pool) + r.off;
+    const size_t N = (size_t)r.code->dev.N;
+    size_t o = 0;
+    r.o_ws = o; o += a256(r.ws_bytes);
+    r.o_obs = o; o += a256(r.obs.size() * 4);
+    r.o_fp = o; o += a256(r.fparam.size() * 4);
+    r.o_state = o; o += a256((size_t)r.F * 4);
+    r.o_x = o; o += a256((size_t)r.F * N);
+    r.o_it = o; o += a256((size_t)r.F * 4);
+    r.o_cv = o;
+    cudaError_t e = cudaMemcpyAsync(base + r.o_obs, r.obs.data(), r.obs.size() * 4, cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess && !r.fparam.empty())
+        e = cudaMemcpyAsync(base + r.o_fp, r.fparam.data(), r.fparam.size() * 4, cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + r.o_state, 0, (size_t)r.F * 4, S->stream);
+    if (e != cudaSuccess) return GFBP_ECUDA;
+    gfbp_channel ch = r.ch;
+    ch.frame_param = r.fparam.empty() ? nullptr : reinterpret_cast<const float*>(base + r.o_fp);
+    gfbp_prior pr{};
+    if (r.markov) { pr.kind = GFBP_PRIOR_MARKOV; pr.T = r.T.data(); pr.K = r.K; pr.src_pos = r.src_pos.data(); }
+    const int method = r.code->dev.q <= 16 ? kDirect : kTransform;
+    e = batch_prepare_item(r.A, base + r.o_ws, r.code, r.F, reinterpret_cast<const float*>(base + r.o_obs), ch,
+                           (gfbp_schedule)r.schedule, r.markov ? &pr : nullptr, r.max_iter, base + r.o_x,
+                           reinterpret_cast<int32_t*>(base + r.o_it), base + r.o_cv, nullptr, method, nullptr,
+                           S->stream);
+    if (e != cudaSuccess) return GFBP_EINVAL;
+    r.A.fstate = reinterpret_cast<int*>(base + r.o_state);
+    r.A.round_iters = S->round_iters;
+    e = launch_channel(r.A, S->stream);
+    if (e == cudaSuccess && r.A.markov) e = launch_fill_prior(r.A, S->stream);
+    if (e == cudaSuccess && r.schedule == GFBP_SUS) e = launch_init_dev(r.A, S->stream);
+    return e == cudaSuccess ? GFBP_OK : GFBP_ECUDA;
+}
+
+// Build and launch one schedule's mixed kernel over the resident requests.
+cudaError_t launch_round(gfbp_server* S, int schedule, const std::vector<Req*>& rs) {
+    std::vector<DecodeArgs> items;
+    std::vector<int> prefix(1, 0), variant;
+    int owner[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    for (Req* r : rs) {
+        if (r->schedule != schedule) continue;
+        const int pf = r->code->dev.p - 1;
+        if (owner[pf] < 0) owner[pf] = (int)items.size();
+        items.push_back(r->A);
+        prefix.push_back(prefix.back() + r->F);
+        variant.push_back(tuned_variant(r->code, schedule));
+    }
+    if (items.empty()) return cudaSuccess;
+    LaunchBufs& B = S->bufs[schedule];
+    const int n = (int)items.size();
+    const size_t a_args = a256(sizeof(DecodeArgs) * (size_t)n), a_int = a256(sizeof(int) * (size_t)(n + 1));
+    if (n > B.cap) {
+        if (B.dmem) cudaFree(B.dmem);
+        B.cap = std::max(n, 2 * B.cap);
+        const size_t cargs = a256(sizeof(DecodeArgs) * (size_t)B.cap), cint = a256(sizeof(int) * (size_t)(B.cap + 1));
+        cudaError_t e = cudaMalloc(&B.dmem, cargs + 2 * cint + 512);
+        if (e != cudaSuccess) { B.cap = 0; B.dmem = nullptr; return e; }
+    }
+    const size_t cargs = a256(sizeof(DecodeArgs) * (size_t)B.cap), cint = a256(sizeof(int) * (size_t)(B.cap + 1));
+    (void)a_args;
+    (void)a_int;
+    uint8_t* base = static_cast<uint8_t*>(B.dmem);
+    MixedLaunch& m = B.m;
+    m.d_args = reinterpret_cast<DecodeArgs*>(base);
+    m.d_prefix = reinterpret_cast<int*>(base + cargs);
+    m.d_variant = reinterpret_cast<int*>(base + cargs + cint);
+    m.d_counter = reinterpret_cast<int*>(base + cargs + 2 * cint);
+    m.d_field = reinterpret_cast<int*>(base + cargs + 2 * cint + 256);
+    m.n_items = n;
+    m.total = prefix.back();
+    m.schedule = schedule;
+    cudaError_t e = cudaMemcpyAsync(m.d_args, items.data(), sizeof(DecodeArgs) * n, cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_prefix, prefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_variant, variant.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_field, owner, sizeof(owner), cudaMemcpyHostToDevice, S->stream);
+    if (e != cudaSuccess) return e;
+    mixed_shape(m);
+    return mixed_launch(m, S->stream);
+}
+
+void worker_main(gfbp_server* S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<Req*> admitted;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait_for(lk, std::chrono::milliseconds(20), [&] {
+                return S->stop || !S->queue.empty() || !S->resident.empty();
+            });
+            if (S->stop && S->queue.empty() && S->resident.empty()) break;
+            // admission in arrival order while the footprint fits
+            while (!S->queue.empty()) {
+                Req* r = S->queue.front();
+                size_t off = 0;
+                if (!S->alloc->alloc(r->bytes, &off)) break;
+                S->queue.pop_front();
+                r->off = off;
+                r->t_admit = Clock::now();
+                admitted.push_back(r);
+            }
+        }
+        std::vector<Req*> failed;
+        for (Req* r : admitted) {
+            r->status = setup(S, *r);
+            if (r->status != GFBP_OK) failed.push_back(r);
+        }
+        std::vector<Req*> round;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (Req* r : admitted)
+                if (r->status == GFBP_OK) {
+                    r->state = 1;
+                    S->resident.push_back(r);
+                }
+            round = S->resident;
+            S->peak_resident = std::max(S->peak_resident, (int)S->resident.size());
+            S->peak_bytes = std::max(S->peak_bytes, S->alloc->used());
+        }
+        for (Req* r : failed) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->alloc->release(r->off, r->bytes);
+            r->state = 3;
+            r->t_done = Clock::now();
+            S->cv_done.notify_all();
+        }
+        if (round.empty()) continue;
+        cudaError_t e = launch_round(S, GFBP_SUS, round);
+        if (e == cudaSuccess) e = launch_round(S, GFBP_PUS, round);
+        // frame states of every resident request
+        std::vector<std::vector<int>> st(round.size());
+        for (size_t i = 0; i < round.size() && e == cudaSuccess; i++) {
+            st[i].resize(round[i]->F);
+            e = cudaMemcpyAsync(st[i].data(), round[i]->A.fstate, sizeof(int) * round[i]->F, cudaMemcpyDeviceToHost,
+                                S->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+        std::vector<Req*> done;
+        for (size_t i = 0; i < round.size(); i++) {
+            Req* r = round[i];
+            r->rounds++;
+            bool all = e == cudaSuccess;
+            for (int f = 0; f < r->F && all; f++) all = (st[i][f] >> 30) != 0;
+            if (all || e != cudaSuccess) done.push_back(r);
+        }
+        for (Req* r : done) {
+            const uint8_t* base = static_cast<const uint8_t*>(S->pool) + r->off;
+            const size_t N = (size_t)r->code->dev.N;
+            if (e == cudaSuccess) {
+                cudaMemcpyAsync(r->hx, base + r->o_x, (size_t)r->F * N, cudaMemcpyDeviceToHost, S->stream);
+                cudaMemcpyAsync(r->hit, base + r->o_it, (size_t)r->F * 4, cudaMemcpyDeviceToHost, S->stream);
+                cudaMemcpyAsync(r->hconv, base + r->o_cv, (size_t)r->F, cudaMemcpyDeviceToHost, S->stream);
+            }
+        }
+        if (!done.empty()) cudaStreamSynchronize(S->stream);
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->rounds++;
+        for (Req* r : done) {
+            r->state = e == cudaSuccess ? 2 : 3;
+            r->status = e == cudaSuccess ? GFBP_OK : GFBP_ECUDA;
+            r->t_done = Clock::now();
+            S->alloc->release(r->off, r->bytes);
+            S->resident.erase(std::find(S->resident.begin(), S->resident.end(), r));
+            S->completed++;
+        }
+        if (!done.empty()) S->cv_done.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" gfbp_status gfbp_server_create(size_t hbm_budget_bytes, int32_t round_iters, gfbp_server** out) {
+    if (!out || hbm_budget_bytes < (1u << 20) || round_iters < 1) {
+        set_error("gfbp_server_create: need a budget >= 1 MiB, round_iters >= 1 and an output handle");
+        return GFBP_EINVAL;
+    }
+    *out = nullptr;
+    gfbp_server* S = new (std::nothrow) gfbp_server();
+    if (!S) { set_error("gfbp_server_create: out of host memory"); return GFBP_ENOMEM; }
+    S->budget = hbm_budget_bytes;
+    S->round_iters = round_iters;
+    cudaGetDevice(&S->device);
+    cudaError_t e = cudaMalloc(&S->pool, hbm_budget_bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        set_error(std::string("gfbp_server_create: ") + cudaGetErrorString(e));
+        if (S->pool) cudaFree(S->pool);
+        delete S;
+        return e == cudaErrorMemoryAllocation ? GFBP_ENOMEM : GFBP_ECUDA;
+    }
+    S->alloc.reset(new PoolAlloc(hbm_budget_bytes));
+    S->worker = std::thread(worker_main, S);
+    *out = S;
+    return GFBP_OK;
+}
+
+extern "C" gfbp_status gfbp_server_submit(gfbp_server* S, const gfbp_request* q, uint64_t* id) {
+    if (!S || !q || !id || !q->code || q->n_frames < 1 || !q->obs || !q->x_hat || !q->iters || !q->converged ||
+        q->max_iter < 1 || (q->schedule != GFBP_PUS && q->schedule != GFBP_SUS)) {
+        set_error("gfbp_server_submit: bad request");
+        return GFBP_EINVAL;
+    }
+    const gfbp_code* c = q->code;
+    if (c->dev.dcmax > 6 || c->dev.dvmax > 3) {
+        set_error("gfbp_server_submit: served codes take row degree <= 6 and column degree <= 3");
+        return GFBP_EUNSUPPORTED;
+    }
+    std::unique_ptr<Req> r(new Req());
+    r->code = c;
+    r->F = q->n_frames;
+    r->schedule = q->schedule;
+    r->max_iter = q->max_iter;
+    r->ch = q->channel;
+    const int p = c->dev.p, Qn = c->dev.q;
+    const size_t per = q->channel.kind == GFBP_LOGLIK ? (size_t)Qn : (size_t)p;
+    r->obs.assign(q->obs, q->obs + (size_t)q->n_frames * c->dev.N * per);
+    if (q->channel.frame_param) r->fparam.assign(q->channel.frame_param, q->channel.frame_param + q->n_frames);
+    r->ch.frame_param = nullptr;
+    if (q->prior && q->prior->kind == GFBP_PRIOR_MARKOV) {
+        if (!q->prior->T || q->prior->K < 1 || q->prior->K > c->dev.N) {
+            set_error("gfbp_server_submit: Markov prior needs T and 1 <= K <= N");
+            return GFBP_EINVAL;
+        }
+        r->markov = true;
+        r->T.assign(q->prior->T, q->prior->T + (size_t)Qn * Qn);
+        r->K = q->prior->K;
+        r->src_pos.resize(r->K);
+        for (int i = 0; i < r->K; i++) r->src_pos[i] = q->prior->src_pos ? q->prior->src_pos[i] : i;
+    }
+    r->hx = q->x_hat;
+    r->hit = q->iters;
+    r->hconv = q->converged;
+    r->bytes = footprint(*r, &r->ws_bytes);
+    if (r->bytes > S->budget) {
+        set_error("gfbp_server_submit: the request's device footprint (" + std::to_string(r->bytes) +
+                  " bytes) exceeds the server budget");
+        return GFBP_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->draining || S->stop) {
+        set_error("gfbp_server_submit: the server is draining");
+        return GFBP_EBUSY;
+    }
+    const int pf = p - 1;
+    if (S->field_poly[pf] && S->field_poly[pf] != c->poly) {
+        set_error("gfbp_server_submit: codes of the same field size must use the same field polynomial");
+        return GFBP_EUNSUPPORTED;
+    }
+    S->field_poly[pf] = c->poly;
+    r->id = S->next_id++;
+    r->t_submit = Clock::now();
+    *id = r->id;
+    S->queue.push_back(r.get());
+    S->reqs[r->id] = std::move(r);
+    S->cv_work.notify_one();
+    return GFBP_OK;
+}
+
+extern "C" gfbp_status gfbp_server_wait(gfbp_server* S, uint64_t id, int64_t timeout_us, gfbp_result* res) {
+    if (!S) { set_error("gfbp_server_wait: NULL server"); return GFBP_EINVAL; }
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) { set_error("gfbp_server_wait: unknown request id"); return GFBP_EINVAL; }
+    Req* r = it->second.get();
+    const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+    while (r->state < 2) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && r->state < 2) {
+            set_error("gfbp_server_wait: timed out");
+            return GFBP_ETIMEOUT;
+        }
+    }
+    if (res) {
+        res->latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
+        res->queue_us = std::chrono::duration<double, std::micro>(r->t_admit - r->t_submit).count();
+        res->rounds = r->rounds;
+    }
+    const gfbp_status st = r->state == 2 ? GFBP_OK : r->status;
+    S->reqs.erase(it);
+    if (st != GFBP_OK) set_error("gfbp_server_wait: the request failed on the device");
+    return st;
+}
+
+extern "C" gfbp_status gfbp_server_stats(gfbp_server* S, gfbp_server_stats_t* out) {
+    if (!S || !out) { set_error("gfbp_server_stats: NULL argument"); return GFBP_EINVAL; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->queued = (int32_t)S->queue.size();
+    out->resident = (int32_t)S->resident.size();
+    out->peak_resident = S->peak_resident;
+    out->rounds = S->rounds;
+    out->completed = S->completed;
+    out->bytes_in_use = S->alloc->used();
+    out->peak_bytes = S->peak_bytes;
+    return GFBP_OK;
+}
+
+extern "C" gfbp_status gfbp_server_drain(gfbp_server* S) {
+    if (!S) { set_error("gfbp_server_drain: NULL server"); return GFBP_EINVAL; }
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->draining = true;
+    S->cv_work.notify_one();
+    while (!S->queue.empty() || !S->resident.empty()) S->cv_done.wait_for(lk, std::chrono::milliseconds(20));
+    return GFBP_OK;
+}
+
+extern "C" void gfbp_server_destroy(gfbp_server* S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->draining = true;
+    }
+    S->cv_work.notify_one();
+    if (S->worker.joinable()) S->worker.join();
+    for (auto& b : S->bufs)
+        if (b.dmem) cudaFree(b.dmem);
+    cudaStreamDestroy(S->stream);
+    cudaFree(S->pool);
+    delete S;
+}

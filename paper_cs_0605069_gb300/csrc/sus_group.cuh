@@ -191,7 +191,14 @@ __device__ __forceinline__ void sus_group_frame(const DecodeArgs& A, int f, cons
     const uint8_t* zf = A.syn ? A.syn + (size_t)f * M : nullptr;
     uint8_t* xh = A.xhat + (size_t)f * N;
 
-    int t = 1, ok = 0;
+    int t0 = 0;   // iterations already done (resumable decoding)
+    if (A.fstate) {
+        const int st = A.fstate[f];
+        if (st >> 30) return;
+        t0 = st;
+    }
+    int t = t0 + 1, ok = 0;
+    bool fin = false;
     for (;; t++) {
         ColBuf<Q, PF ? DC : 1, PF ? DV : 1> cur, nxt;
         if constexpr (PF) load_col<Q, DC, DV>(cur, A, slab, 0, g);
@@ -278,11 +285,15 @@ __device__ __forceinline__ void sus_group_frame(const DecodeArgs& A, int f, cons
             uint8_t* tr = A.trace + ((size_t)f * A.max_iter + (t - 1)) * N;
             for (int j = g; j < N; j += G) tr[j] = xh[j];
         }
-        if ((ok && A.early_stop) || t >= A.max_iter) break;
+        if ((ok && A.early_stop) || t >= A.max_iter) {
+            fin = true;
+            break;
+        }
         if (A.markov) {
             for (int i = 0; i < A.K; i++) markov_prior<Q>(A, f, i, A.P + ((size_t)f * A.K + i) * Q, mask, g);
             __syncwarp(mask);
         }
+        if (A.fstate && t - t0 >= A.round_iters) break;
     }
     if (A.step && A.markov && A.prior_out) {
         for (int i = 0; i < A.K; i++) markov_prior<Q>(A, f, i, A.prior_out + ((size_t)f * A.K + i) * Q, mask, g);
@@ -292,8 +303,11 @@ __device__ __forceinline__ void sus_group_frame(const DecodeArgs& A, int f, cons
             A.trace[(size_t)f * A.max_iter * N + o] = 255;
     }
     if (g == 0) {
-        if (A.iters) A.iters[f] = t;
-        A.conv[f] = (uint8_t)ok;
+        if (!A.fstate || fin) {
+            if (A.iters) A.iters[f] = t;
+            A.conv[f] = (uint8_t)ok;
+        }
+        if (A.fstate) A.fstate[f] = fin ? (t | (1 << 30)) : t;
     }
 }
 

@@ -180,7 +180,14 @@ __device__ __forceinline__ void sus_team_frame(const DecodeArgs& A, int f, const
     const uint8_t* zf = A.syn ? A.syn + (size_t)f * M : nullptr;
     uint8_t* xh = A.xhat + (size_t)f * N;
 
-    int t = 1, ok = 0;
+    int t0 = 0;   // iterations already done (resumable decoding)
+    if (A.fstate) {
+        const int st = A.fstate[f];
+        if (st >> 30) return;
+        t0 = st;
+    }
+    int t = t0 + 1, ok = 0;
+    bool fin = false;
     for (;; t++) {
         SlotBuf<Q, DC> cur, nxt;
         slot_load<Q, DC>(cur, A, slab, f, 0, k, g);
@@ -294,11 +301,15 @@ __device__ __forceinline__ void sus_team_frame(const DecodeArgs& A, int f, const
             uint8_t* tr = A.trace + ((size_t)f * A.max_iter + (t - 1)) * N;
             for (int jj = tl; jj < N; jj += TEAM) tr[jj] = xh[jj];
         }
-        if ((ok && A.early_stop) || t >= A.max_iter) break;
+        if ((ok && A.early_stop) || t >= A.max_iter) {
+            fin = true;
+            break;
+        }
         if (A.markov) {
             for (int i = 0; i < A.K; i++) team_prior<Q, TEAM>(A, f, i, A.P + ((size_t)f * A.K + i) * Q, tmask, tl);
             __syncwarp(tmask);
         }
+        if (A.fstate && t - t0 >= A.round_iters) break;
     }
     if (A.step && A.markov && A.prior_out) {
         for (int i = 0; i < A.K; i++)
@@ -309,8 +320,11 @@ __device__ __forceinline__ void sus_team_frame(const DecodeArgs& A, int f, const
             A.trace[(size_t)f * A.max_iter * N + o] = 255;
     }
     if (tl == 0) {
-        if (A.iters) A.iters[f] = t;
-        A.conv[f] = (uint8_t)ok;
+        if (!A.fstate || fin) {
+            if (A.iters) A.iters[f] = t;
+            A.conv[f] = (uint8_t)ok;
+        }
+        if (A.fstate) A.fstate[f] = fin ? (t | (1 << 30)) : t;
     }
 }
 

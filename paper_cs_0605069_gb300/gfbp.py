@@ -26,7 +26,9 @@ CHECK_METHOD = {"auto": 0, "transform": 1, "direct": 2}
 # Functions declared in include/gfbp.h (the CPU test checks that every one is exported).
 EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info",
            "gfbp_workspace_size", "gfbp_decode", "gfbp_step", "gfbp_decode_noalloc",
-           "gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_batch_destroy", "gfbp_autotune")
+           "gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_batch_destroy", "gfbp_autotune",
+           "gfbp_server_create", "gfbp_server_submit", "gfbp_server_wait", "gfbp_server_stats",
+           "gfbp_server_drain", "gfbp_server_destroy")
 
 
 class GfbpError(RuntimeError):
@@ -321,3 +323,94 @@ def autotune(code: Code, obs, channel: str, param: float = 0.0, schedule: str = 
                                    SCHEDULE[schedule], C.byref(pr), int(max_iter), _stream(stream), C.byref(v)),
         "gfbp_autotune")
     return v.value
+
+
+class gfbp_request(C.Structure):
+    _fields_ = [("code", C.c_void_p), ("n_frames", C.c_int32), ("obs", C.c_void_p), ("channel", gfbp_channel),
+                ("prior", C.c_void_p), ("schedule", C.c_int32), ("max_iter", C.c_int32), ("x_hat", C.c_void_p),
+                ("iters", C.c_void_p), ("converged", C.c_void_p)]
+
+
+class gfbp_result(C.Structure):
+    _fields_ = [("latency_us", C.c_double), ("queue_us", C.c_double), ("rounds", C.c_int32)]
+
+
+class gfbp_server_stats_t(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("resident", C.c_int32), ("peak_resident", C.c_int32),
+                ("rounds", C.c_int64), ("completed", C.c_int64), ("bytes_in_use", C.c_size_t),
+                ("peak_bytes", C.c_size_t)]
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_typed", False):
+        P = C.c_void_p
+        L.gfbp_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(C.c_void_p)]
+        L.gfbp_server_submit.argtypes = [P, C.POINTER(gfbp_request), C.POINTER(C.c_uint64)]
+        L.gfbp_server_wait.argtypes = [P, C.c_uint64, C.c_int64, C.POINTER(gfbp_result)]
+        L.gfbp_server_stats.argtypes = [P, C.POINTER(gfbp_server_stats_t)]
+        L.gfbp_server_drain.argtypes = [P]
+        L.gfbp_server_destroy.argtypes = [P]
+        L.gfbp_server_destroy.restype = None
+        for fn in ("gfbp_server_create", "gfbp_server_submit", "gfbp_server_wait", "gfbp_server_stats",
+                   "gfbp_server_drain"):
+            getattr(L, fn).restype = C.c_int
+        L._server_typed = True
+    return L
+
+
+class Server:
+    """gfbp_server: continuous batching of decode requests with host inputs and
+    outputs (numpy arrays)."""
+
+    def __init__(self, hbm_budget_bytes: int, round_iters: int = 8):
+        h = C.c_void_p()
+        _ok(_server_lib().gfbp_server_create(int(hbm_budget_bytes), int(round_iters), C.byref(h)),
+            "gfbp_server_create")
+        self.handle = h
+        self._pending = {}
+
+    def submit(self, code: Code, obs, channel: str = "bsc", param: float = 0.0, frame_param=None, T=None,
+               K: int = 0, schedule: str = "sus", max_iter: int = 100) -> int:
+        obs = np.ascontiguousarray(obs, dtype=np.float32)
+        F = int(obs.shape[0])
+        out = dict(x_hat=np.zeros((F, code.N), np.uint8), iters=np.zeros(F, np.int32),
+                   converged=np.zeros(F, np.uint8))
+        fp = None if frame_param is None else np.ascontiguousarray(frame_param, dtype=np.float32)
+        pr, keep = _prior(T, K, None)
+        req = gfbp_request(code.handle, F, obs.ctypes.data,
+                           gfbp_channel(CHANNEL[channel], float(param), None if fp is None else fp.ctypes.data),
+                           C.cast(C.pointer(pr), C.c_void_p) if T is not None else None, SCHEDULE[schedule],
+                           int(max_iter), out["x_hat"].ctypes.data, out["iters"].ctypes.data,
+                           out["converged"].ctypes.data)
+        rid = C.c_uint64()
+        _ok(_server_lib().gfbp_server_submit(self.handle, C.byref(req), C.byref(rid)), "gfbp_server_submit")
+        self._pending[rid.value] = (out, obs, fp, pr, keep)
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = 60.0):
+        res = gfbp_result()
+        _ok(_server_lib().gfbp_server_wait(self.handle, C.c_uint64(rid), int(timeout_s * 1e6), C.byref(res)),
+            "gfbp_server_wait")
+        out = self._pending.pop(rid)[0]
+        out.update(latency_us=res.latency_us, queue_us=res.queue_us, rounds=res.rounds)
+        return out
+
+    def stats(self):
+        st = gfbp_server_stats_t()
+        _ok(_server_lib().gfbp_server_stats(self.handle, C.byref(st)), "gfbp_server_stats")
+        return {k: getattr(st, k) for k, _ in gfbp_server_stats_t._fields_}
+
+    def drain(self):
+        _ok(_server_lib().gfbp_server_drain(self.handle), "gfbp_server_drain")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _server_lib().gfbp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
