@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=0, help="override the workload's max_iter (profiling cases)")
     ap.add_argument("--method", default="auto", choices=["auto", "direct", "transform"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve"],
+                    help="batch: the GF(16) N=1000 benchmark (default); mixed: frames of 12 (q, N) classes in one "
+                         "persistent launch; serve: Poisson arrivals to the continuous-batching server")
+    ap.add_argument("--duration", type=float, default=6.0, help="serve: seconds per offered load")
     return ap.parse_args()
 
 
@@ -189,6 +193,14 @@ def main():
     rank, world, local = dist_info()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "mixed":
+        from bench_modes import run_mixed
+        run_mixed(args)
+        return
+    if args.workload == "serve":
+        from bench_modes import run_serve
+        run_serve(args)
         return
     import torch
     torch.cuda.set_device(local)
