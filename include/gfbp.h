@@ -135,6 +135,12 @@ typedef struct {
     void* kernel_events[2];  /* optional cudaEvent_t pair, recorded on `stream` right before
                                 and right after the schedule kernel (for timing it alone) */
     int32_t check_method;    /* gfbp_check_method for the horizontal pass (Eq. 3) */
+    int32_t sus_width;       /* SUS with q <= 16, column degree <= 4, row degree <= 8:
+                                lane teams per frame, 1, 2, 4 or 8 (0 = chosen from
+                                the frame count).  Teams > 1 update columns that share
+                                no check at the same time; every column still sees the
+                                values of the sequential order, so results are the
+                                same bit for bit.  Ignored elsewhere. */
 } gfbp_options;
 
 /*

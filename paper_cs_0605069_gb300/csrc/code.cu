@@ -113,6 +113,9 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     // column j shares a check with column j-1 (SUS prefetch must then reload)
     std::vector<int4> cinfo(E);
     std::vector<uint8_t> cdep(N, 0);
+    // and the last earlier column that shares a check with column j (-1 if
+    // none): SUS may run column j once every column up to that one is done
+    std::vector<int> cpred(N, -1);
     for (int j = 0; j < N; j++) {
         for (int k = colptr[j]; k < colptr[j + 1]; k++) {
             const int e = cedge[k], i = erow[e];
@@ -120,16 +123,18 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
             if (j > 0)
                 for (int k2 = colptr[j - 1]; k2 < colptr[j]; k2++)
                     if (erow[cedge[k2]] == i) cdep[j] = 1;
+            for (int e2 = rowptr[i]; e2 < rowptr[i + 1]; e2++)
+                if (ecol[e2] < j) cpred[j] = std::max(cpred[j], ecol[e2]);
         }
     }
 
-    // one device allocation: rowptr | colptr | ecol | erow | cedge | eh | gexp | glog | cinfo | cdep
-    constexpr int NA = 10;
+    // one device allocation: rowptr | colptr | ecol | erow | cedge | eh | gexp | glog | cinfo | cdep | cpred
+    constexpr int NA = 11;
     size_t off[NA], total = 0;
     const size_t sz[NA] = {sizeof(int) * (size_t)(M + 1), sizeof(int) * (size_t)(N + 1), sizeof(int) * (size_t)E,
                            sizeof(int) * (size_t)E,       sizeof(int) * (size_t)E,       (size_t)E,
                            512,                           256,                           sizeof(int4) * (size_t)E,
-                           (size_t)N};
+                           (size_t)N,                     sizeof(int) * (size_t)N};
     for (int k = 0; k < NA; k++) { off[k] = total; total += align256(sz[k] ? sz[k] : 1); }
     std::vector<uint8_t> host(total, 0);
     std::memcpy(host.data() + off[0], rowptr.data(), sz[0]);
@@ -144,6 +149,7 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     std::memcpy(host.data() + off[6], ex, 512);
     std::memcpy(host.data() + off[7], lg, 256);
     std::memcpy(host.data() + off[9], cdep.data(), sz[9]);
+    std::memcpy(host.data() + off[10], cpred.data(), sz[10]);
 
     gfbp_code* c = new (std::nothrow) gfbp_code();
     if (!c) { set_error("gfbp_code_create: out of host memory"); return GFBP_ENOMEM; }
@@ -174,6 +180,7 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     d.glog = base + off[7];
     d.cinfo = reinterpret_cast<const int4*>(base + off[8]);
     d.cdep = base + off[9];
+    d.cpred = reinterpret_cast<const int*>(base + off[10]);
     c->poly = poly;
     *out = c;
     return GFBP_OK;

@@ -303,6 +303,11 @@ gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const flo
         return GFBP_EINVAL;
     }
     A.method = (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > 16)) ? kTransform : kDirect;
+    A.width = opt ? opt->sus_width : 0;
+    if (A.width != 0 && A.width != 1 && A.width != 2 && A.width != 4 && A.width != 8) {
+        set_error("sus_width must be 0, 1, 2, 4 or 8");
+        return GFBP_EINVAL;
+    }
     return GFBP_OK;
 }
 

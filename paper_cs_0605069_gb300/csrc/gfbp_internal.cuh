@@ -41,6 +41,7 @@ struct CodeDev {
     const uint8_t* glog; // [256] log_x(a) for a != 0
     const int4* cinfo;   // [E] per column slot: {edge, row start, row degree | h << 8, row}
     const uint8_t* cdep; // [N] 1 when column j shares a check with column j-1
+    const int* cpred;    // [N] last column k < j sharing a check with column j, -1 if none
 };
 
 struct DecodeArgs {
@@ -82,6 +83,7 @@ struct DecodeArgs {
     // bit 30 set once the frame has stopped; NULL = whole decode in one launch
     int* fstate;
     int round_iters;       // resumable decoding: iterations per launch
+    int width;             // SUS team kernels: teams per frame (0 = automatic)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -567,6 +569,8 @@ enum Method { kDirect = 0, kTransform = 1 };
 cudaError_t launch_channel(const DecodeArgs& A, cudaStream_t s);
 bool sus_team_eligible(const DecodeArgs& A);
 cudaError_t launch_sus_team(const DecodeArgs& A, int num_sms, cudaStream_t s);
+cudaError_t launch_sus_wave(const DecodeArgs& A, int width, int num_sms, cudaStream_t s);
+int sus_auto_width(const DecodeArgs& A, int num_sms);
 cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s);

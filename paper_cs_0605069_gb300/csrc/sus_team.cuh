@@ -160,12 +160,15 @@ __device__ __forceinline__ void team_prior(const DecodeArgs& A, int f, int i, fl
     if (b < Q) out[b] = (s > 0.f && s <= 3.0e38f) ? P / s : 1.0f / Q;
 }
 
-// One frame's whole SUS decode by the calling team (all iterations, the test,
-// the Markov update and the outputs).  s_mul / s_div: the field's multiply
-// and divide-by-h tables; sa: this slot's shared scratch (2q + 4 floats).
+// Steps 1-2 of SUS for column j by the calling team: the r_ij of every check
+// of the column (slot k: the column's k-th check) from the stored vectors in
+// `cur`, then Q_j (hard decision, posterior, Markov source posterior) and the
+// new stored q_ij.  s_mul / s_div: the field's multiply and divide-by-h
+// tables; sa: this slot's shared scratch (2q + 4 floats).
 template <int Q, int DC>
-__device__ __forceinline__ void sus_team_frame(const DecodeArgs& A, int f, const uint8_t* s_mul,
-                                               const uint8_t* s_div, float* sa) {
+__device__ __forceinline__ void team_column(const DecodeArgs& A, int f, int j, const SlotBuf<Q, DC>& cur,
+                                            const uint8_t* s_mul, const uint8_t* s_div, float* sa, float* slab,
+                                            const uint8_t* zf, uint8_t* xh) {
     using TL = TeamLay<Q>;
     constexpr int GS = TL::GS, V = TL::V, TEAM = TL::TEAM;
     const int tl = threadIdx.x & (TEAM - 1);
@@ -174,6 +177,109 @@ __device__ __forceinline__ void sus_team_frame(const DecodeArgs& A, int f, const
     const unsigned tmask = lanes_mask<TEAM>();
     const unsigned smask = lanes_mask<GS>();
     const int team_lane0 = (threadIdx.x & 31) & ~(TEAM - 1);
+    const int N = A.c.N;
+    const long long E = A.c.E;
+    const int d = cur.d;
+    const bool act = k < d;
+    const int4 in = cur.info;
+    const int own = act ? in.x - in.y : 0;
+    const int dc = act ? (in.z & 255) : 1;
+    const int h = act ? ((in.z >> 8) & 255) : 1;
+    const int z = (act && zf) ? (zf[in.w] & (Q - 1)) : 0;
+    // step 1: distribution of the XOR-sum of the check's other edges,
+    // folded in neighbour order (the same instruction stream in every slot)
+    const int c = dc - 1;
+    float U[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) U[v] = (g * V + v) == 0 ? 1.f : 0.f;
+#pragma unroll
+    for (int n = 0; n < DC - 1; n++) {
+        if (n < c) {
+            float Y[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) Y[v] = (n >= own) ? cur.D[n + 1][v] : cur.D[n][v];
+            if (n == 0) {
+#pragma unroll
+                for (int v = 0; v < V; v++) U[v] = Y[v];
+            } else {
+                stv<V>(sa + g * V, U);
+                stv<V>(sa + Q + g * V, Y);
+                __syncwarp(smask);
+                xconv_team<Q, V>(U, sa, sa + Q, g);
+                __syncwarp(smask);
+            }
+        }
+    }
+    // r_ij[a] = s[z XOR h a], normalised
+    stv<V>(sa + g * V, U);
+    __syncwarp(smask);
+    float R[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) R[v] = sa[(z ^ s_mul[h * Q + g * V + v]) & (Q - 1)];
+    __syncwarp(smask);
+    slot_normalise<Q, GS, V>(R, smask);
+    if (!act) {
+#pragma unroll
+        for (int v = 0; v < V; v++) R[v] = 1.f;
+    }
+    // step 2: products over the other slots' r at the same entries
+    float p[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) p[v] = cur.L[v];
+    if (A.markov) {
+        const int si = A.src_index[j];
+        if (si >= 0) {
+            float P[V];
+            ldv<V>(P, A.P + ((size_t)f * A.K + si) * Q + g * V);
+#pragma unroll
+            for (int v = 0; v < V; v++) p[v] *= P[v];
+            slot_normalise<Q, GS, V>(p, smask);
+        }
+    }
+    float other[V], all[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) { other[v] = p[v]; all[v] = p[v]; }
+#pragma unroll
+    for (int k2 = 0; k2 < kSlots; k2++) {
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const float r2 = __shfl_sync(tmask, R[v], team_lane0 + k2 * GS + g);
+            all[v] *= r2;
+            if (k2 != k) other[v] *= r2;
+        }
+    }
+    slot_normalise<Q, GS, V>(all, smask);
+    if (k == 0) {
+        const int a = slot_argmax<GS, V>(all, smask, g);
+        if (g == 0) xh[j] = (uint8_t)a;
+        if (A.post) stv<V>(A.post + ((size_t)f * N + j) * Q + g * V, all);
+        if (A.markov) {
+            const int si = A.src_index[j];
+            if (si >= 0) stv<V>(A.Qsrc + ((size_t)f * A.K + si) * Q + g * V, all);
+        }
+    }
+    slot_normalise<Q, GS, V>(other, smask);
+    if (act && A.step) stv<V>(A.msg_io + ((size_t)f * E + in.x) * Q + g * V, other);
+    // stored form: qt[y] = q[h^-1 y]
+    stv<V>(sa + g * V, other);
+    __syncwarp(smask);
+#pragma unroll
+    for (int v = 0; v < V; v++) other[v] = sa[s_div[h * Q + g * V + v]];
+    __syncwarp(smask);
+    if (act) stv<V>(slab + (size_t)in.x * Q + g * V, other);
+}
+
+// One frame's whole SUS decode by the calling team (all iterations, the test,
+// the Markov update and the outputs).
+template <int Q, int DC>
+__device__ __forceinline__ void sus_team_frame(const DecodeArgs& A, int f, const uint8_t* s_mul,
+                                               const uint8_t* s_div, float* sa) {
+    using TL = TeamLay<Q>;
+    constexpr int GS = TL::GS, TEAM = TL::TEAM;
+    const int tl = threadIdx.x & (TEAM - 1);
+    const int k = tl / GS;
+    const int g = tl & (GS - 1);
+    const unsigned tmask = lanes_mask<TEAM>();
     const int M = A.c.M, N = A.c.N;
     const long long E = A.c.E;
     float* slab = A.msg + (size_t)f * E * Q;
@@ -193,94 +299,7 @@ __device__ __forceinline__ void sus_team_frame(const DecodeArgs& A, int f, const
         slot_load<Q, DC>(cur, A, slab, f, 0, k, g);
         for (int j = 0; j < N; j++) {
             if (j + 1 < N) slot_load<Q, DC>(nxt, A, slab, f, j + 1, k, g);
-            const int d = cur.d;
-            const bool act = k < d;
-            const int4 in = cur.info;
-            const int own = act ? in.x - in.y : 0;
-            const int dc = act ? (in.z & 255) : 1;
-            const int h = act ? ((in.z >> 8) & 255) : 1;
-            const int z = (act && zf) ? (zf[in.w] & (Q - 1)) : 0;
-            // step 1: distribution of the XOR-sum of the check's other edges,
-            // folded in neighbour order (the same instruction stream in every slot)
-            const int c = dc - 1;
-            float U[V];
-#pragma unroll
-            for (int v = 0; v < V; v++) U[v] = (g * V + v) == 0 ? 1.f : 0.f;
-#pragma unroll
-            for (int n = 0; n < DC - 1; n++) {
-                if (n < c) {
-                    float Y[V];
-#pragma unroll
-                    for (int v = 0; v < V; v++) Y[v] = (n >= own) ? cur.D[n + 1][v] : cur.D[n][v];
-                    if (n == 0) {
-#pragma unroll
-                        for (int v = 0; v < V; v++) U[v] = Y[v];
-                    } else {
-                        stv<V>(sa + g * V, U);
-                        stv<V>(sa + Q + g * V, Y);
-                        __syncwarp(smask);
-                        xconv_team<Q, V>(U, sa, sa + Q, g);
-                        __syncwarp(smask);
-                    }
-                }
-            }
-            // r_ij[a] = s[z XOR h a], normalised
-            stv<V>(sa + g * V, U);
-            __syncwarp(smask);
-            float R[V];
-#pragma unroll
-            for (int v = 0; v < V; v++) R[v] = sa[(z ^ s_mul[h * Q + g * V + v]) & (Q - 1)];
-            __syncwarp(smask);
-            slot_normalise<Q, GS, V>(R, smask);
-            if (!act) {
-#pragma unroll
-                for (int v = 0; v < V; v++) R[v] = 1.f;
-            }
-            // step 2: products over the other slots' r at the same entries
-            float p[V];
-#pragma unroll
-            for (int v = 0; v < V; v++) p[v] = cur.L[v];
-            if (A.markov) {
-                const int si = A.src_index[j];
-                if (si >= 0) {
-                    float P[V];
-                    ldv<V>(P, A.P + ((size_t)f * A.K + si) * Q + g * V);
-#pragma unroll
-                    for (int v = 0; v < V; v++) p[v] *= P[v];
-                    slot_normalise<Q, GS, V>(p, smask);
-                }
-            }
-            float other[V], all[V];
-#pragma unroll
-            for (int v = 0; v < V; v++) { other[v] = p[v]; all[v] = p[v]; }
-#pragma unroll
-            for (int k2 = 0; k2 < kSlots; k2++) {
-#pragma unroll
-                for (int v = 0; v < V; v++) {
-                    const float r2 = __shfl_sync(tmask, R[v], team_lane0 + k2 * GS + g);
-                    all[v] *= r2;
-                    if (k2 != k) other[v] *= r2;
-                }
-            }
-            slot_normalise<Q, GS, V>(all, smask);
-            if (k == 0) {
-                const int a = slot_argmax<GS, V>(all, smask, g);
-                if (g == 0) xh[j] = (uint8_t)a;
-                if (A.post) stv<V>(A.post + ((size_t)f * N + j) * Q + g * V, all);
-                if (A.markov) {
-                    const int si = A.src_index[j];
-                    if (si >= 0) stv<V>(A.Qsrc + ((size_t)f * A.K + si) * Q + g * V, all);
-                }
-            }
-            slot_normalise<Q, GS, V>(other, smask);
-            if (act && A.step) stv<V>(A.msg_io + ((size_t)f * E + in.x) * Q + g * V, other);
-            // stored form: qt[y] = q[h^-1 y]
-            stv<V>(sa + g * V, other);
-            __syncwarp(smask);
-#pragma unroll
-            for (int v = 0; v < V; v++) other[v] = sa[s_div[h * Q + g * V + v]];
-            __syncwarp(smask);
-            if (act) stv<V>(slab + (size_t)in.x * Q + g * V, other);
+            team_column<Q, DC>(A, f, j, cur, s_mul, s_div, sa, slab, zf, xh);
             if (j + 1 < N) {
                 if (nxt.dep) slot_load<Q, DC>(nxt, A, slab, f, j + 1, k, g);
                 cur = nxt;

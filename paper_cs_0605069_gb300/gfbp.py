@@ -48,7 +48,8 @@ class gfbp_prior(C.Structure):
 class gfbp_options(C.Structure):
     _fields_ = [("punct", C.c_void_p), ("syndrome", C.c_void_p), ("post", C.c_void_p),
                 ("xhat_trace", C.c_void_p), ("no_early_stop", C.c_int32), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t), ("kernel_events", C.c_void_p * 2), ("check_method", C.c_int32)]
+                ("workspace_bytes", C.c_size_t), ("kernel_events", C.c_void_p * 2), ("check_method", C.c_int32),
+                ("sus_width", C.c_int32)]
 
 
 def lib() -> C.CDLL:
@@ -155,10 +156,11 @@ def workspace_size(code: Code, n_frames: int, schedule: str = "pus", T=None, K: 
 def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: str = "pus", max_iter: int = 100,
            T=None, K: int = 0, src_pos=None, frame_param=None, punct=None, syndrome=None, post: bool = False,
            trace: bool = False, no_early_stop: bool = False, workspace=None, out=None, stream=None,
-           kernel_events=None, check_method: str = "auto"):
+           kernel_events=None, check_method: str = "auto", sus_width: int = 0):
     """gfbp_decode on CUDA tensors.  obs: float32 [F][N][p] (or [F][N][q] for
     loglik).  Returns dict of device tensors x_hat [F][N] uint8, iters [F]
-    int32, converged [F] uint8 (+ post [F][N][q], trace [F][max_iter][N])."""
+    int32, converged [F] uint8 (+ post [F][N][q], trace [F][max_iter][N]).
+    sus_width: lane teams per frame of the q <= 16 SUS kernels (0 = automatic)."""
     import torch
     F = int(obs.shape[0])
     dev = obs.device
@@ -177,6 +179,7 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
     opt = gfbp_options(_ptr(punct), _ptr(syndrome), _ptr(out.get("post")), _ptr(out.get("trace")),
                        int(no_early_stop), _ptr(workspace), int(workspace.numel()))
     opt.check_method = CHECK_METHOD[check_method]
+    opt.sus_width = int(sus_width)
     if kernel_events is not None:   # (torch.cuda.Event, torch.cuda.Event) timing the schedule kernel alone
         for ev in kernel_events:    # torch creates the CUDA event on its first record
             if not ev.cuda_event:
@@ -192,7 +195,7 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
 
 def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedule: str = "pus", T=None, K: int = 0,
          src_pos=None, prior_in=None, frame_param=None, punct=None, syndrome=None, stream=None,
-         check_method: str = "auto"):
+         check_method: str = "auto", sus_width: int = 0):
     """gfbp_step: one iteration from msg (float32 [F][E][q], updated in place).
     Returns dict(msg, post, x_hat, sat, prior_out)."""
     import torch
@@ -206,6 +209,7 @@ def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedul
     ws = torch.empty(workspace_size(code, F, schedule, T, K, src_pos, step=True), dtype=torch.uint8, device=dev)
     opt = gfbp_options(_ptr(punct), _ptr(syndrome), None, None, 0, _ptr(ws), int(ws.numel()))
     opt.check_method = CHECK_METHOD[check_method]
+    opt.sus_width = int(sus_width)
     ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
     _ok(lib().gfbp_step(code.handle, F, _ptr(obs), ch, SCHEDULE[schedule], C.byref(pr), _ptr(msg), _ptr(prior_in),
                         _ptr(prior_out), _ptr(post), _ptr(x_hat), _ptr(sat), C.byref(opt), _stream(stream)),
@@ -215,7 +219,7 @@ def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedul
 
 def decode_noalloc(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: str = "pus",
                    max_iter: int = 100, T=None, K: int = 0, src_pos=None, frame_param=None, post: bool = False,
-                   check_method: str = "auto", out=None, stream=None):
+                   check_method: str = "auto", out=None, stream=None, sus_width: int = 0):
     """gfbp_decode_noalloc on CUDA tensors: like decode(), with the library's
     static device scratch instead of a workspace (no device allocation inside
     the library; the outputs here are caller tensors)."""
@@ -231,6 +235,7 @@ def decode_noalloc(code: Code, obs, channel: str = "bsc", param: float = 0.0, sc
     pr, _keep = _prior(T, K, src_pos)
     opt = gfbp_options(None, None, _ptr(out.get("post")), None, 0, None, 0)
     opt.check_method = CHECK_METHOD[check_method]
+    opt.sus_width = int(sus_width)
     ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
     _ok(lib().gfbp_decode_noalloc(code.handle, F, _ptr(obs), ch, SCHEDULE[schedule], C.byref(pr), int(max_iter),
                                   _ptr(out["x_hat"]), _ptr(out["iters"]), _ptr(out["converged"]), C.byref(opt),

@@ -1,0 +1,117 @@
+"""SUS with several lane teams per frame against one team per frame.
+
+The multi-team kernel runs columns that share no check at the same time and
+starts a column only after the last earlier column sharing a check with it has
+finished, so every column reads the values of the strictly sequential order:
+its results must equal the single-team kernel's bit for bit (x_hat, iters,
+converged, posteriors, traces, lock-step messages)."""
+import numpy as np
+import pytest
+
+from tests.parity_util import gpu_decode, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_cs_0605069_gb300 import gfbp
+    gfbp.lib()
+    return torch
+
+
+def _same(a, b, what):
+    for k in a:
+        x, y = np.asarray(a[k]), np.asarray(b[k])
+        if x.dtype == np.float32:
+            x, y = x.view(np.uint32), y.view(np.uint32)
+        assert np.array_equal(x, y), f"{what}: {k} differs"
+
+
+def _widths(cd, obs, kind, param, max_iter, widths=(2, 4, 8), **kw):
+    ref = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, sus_width=1, **kw)
+    for w in widths:
+        out = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, sus_width=w, **kw)
+        _same(ref, out, f"width {w}")
+    return ref
+
+
+@pytest.mark.parametrize("name,N,frames,max_iter", [
+    ("gf4_n96_bsc005", None, 64, 60),
+    ("gf16_n1000_awgn", 400, 36, 60),
+    ("gf8_n2000_markov_bsc", 300, 18, 40),
+    ("gf8_n2000_markov_bec", 300, 18, 40),
+])
+def test_wave_equals_single_team(torch_cuda, name, N, frames, max_iter):
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch(name, frames=frames, N=N)
+    cd = gfbp.Code.from_coo(b.code)
+    ref = _widths(cd, b.obs, b.channel, b.param, max_iter, T=b.T, K=b.K)
+    assert ref["iters"].min() >= 1
+
+
+def test_wave_row_degree_8_with_syndrome(torch_cuda):
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    code = W.regular_code(16, 240, dv=4, dc=8, cfg="wave_dc8", encodable=False)
+    rng = np.random.default_rng(7)
+    F = 20
+    x = rng.integers(0, 16, size=(F, code.N))
+    z = code.syndrome(x).astype(np.uint8)   # H x = z holds for the sent word
+    sig = W.ebn0_to_sigma(2.5, rate=0.5)
+    obs = W.biawgn(rng, x, code.p, sig)
+    cd = gfbp.Code.from_coo(code)
+    ref = _widths(cd, obs, "awgn", sig, 50, syndrome=z)
+    assert ref["converged"].sum() > F // 2
+
+
+def test_wave_more_frames_than_resident_ctas(torch_cuda):
+    """Every CTA takes several frames in turn."""
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch("gf4_n96_bsc005", frames=3000)
+    cd = gfbp.Code.from_coo(b.code)
+    _widths(cd, b.obs, b.channel, b.param, 30, widths=(2, 8))
+
+
+def test_wave_code_shorter_than_team_count(torch_cuda):
+    """N = 5 columns, 8 teams: teams without columns must not block."""
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    H = np.array([[1, 2, 0, 3, 1],
+                  [0, 1, 1, 0, 2],
+                  [3, 0, 2, 1, 0]])
+    code = W.code_from_dense(H, 4)
+    rng = np.random.default_rng(3)
+    obs = W.bsc(rng, np.zeros((6, 5), np.int64), code.p, 0.1)
+    cd = gfbp.Code.from_coo(code)
+    _widths(cd, obs, "bsc", 0.1, 20, no_early_stop=True)
+
+
+def test_wave_lockstep_step_equals_single_team(torch_cuda, oracle):
+    import torch
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch("gf8_n2000_markov_bsc", frames=8, N=300)
+    cd = gfbp.Code.from_coo(b.code)
+    F = b.obs.shape[0]
+    msg0 = oracle.initial_messages(b.code, b.obs, b.channel, b.param, T=b.T, K=b.K)
+    _, pi = oracle.markov(b.T, np.full((1, b.code.q), 1.0 / b.code.q))
+    prior = to_dev(np.broadcast_to(pi, (F, b.K, b.code.q)).astype(np.float32).copy())
+    fp = to_dev(np.asarray(b.param, np.float32))
+    outs = {}
+    for w in (1, 4):
+        m = to_dev(msg0.astype(np.float32))
+        o = gfbp.step(cd, to_dev(b.obs, torch.float32), m, channel=b.channel, schedule="sus", T=b.T, K=b.K,
+                      prior_in=prior, frame_param=fp, sus_width=w)
+        torch.cuda.synchronize()
+        outs[w] = {k: v.cpu().numpy() for k, v in o.items() if v is not None}
+    _same(outs[1], outs[4], "step width 4")
+
+
+def test_wave_width_is_validated(torch_cuda):
+    import torch
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch("gf4_n96_bsc005", frames=2)
+    cd = gfbp.Code.from_coo(b.code)
+    with pytest.raises(gfbp.GfbpError):
+        gfbp.decode(cd, to_dev(b.obs, torch.float32), b.channel, float(b.param[0]), schedule="sus", sus_width=3)
