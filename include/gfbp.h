@@ -121,6 +121,20 @@ typedef struct {
  */
 typedef enum { GFBP_CHECK_AUTO = 0, GFBP_CHECK_TRANSFORM = 1, GFBP_CHECK_DIRECT = 2 } gfbp_check_method;
 
+/*
+ * SUS kernel for q = 4, 8, 16 with the DIRECT check node.  Both give the
+ * values of the sequential column order j = 0..N-1, bit for bit:
+ *   TEAMS   lane teams walk the columns in order; with sus_width > 1 teams a
+ *           column starts once the last earlier column sharing a check with
+ *           it is done (column degree <= 4, row degree <= 8).
+ *   LEVELS  the columns are grouped into levels (level(j) = 1 + the highest
+ *           level of the earlier columns sharing a check with j; one level's
+ *           columns share no check) and a level's (column, check) pairs run
+ *           at once, one thread each.
+ *   AUTO    LEVELS where it applies, else TEAMS.
+ */
+typedef enum { GFBP_SUS_AUTO = 0, GFBP_SUS_TEAMS = 1, GFBP_SUS_LEVELS = 2 } gfbp_sus_kernel;
+
 /* Optional inputs and outputs of gfbp_decode / gfbp_step (NULL = defaults). */
 typedef struct {
     const uint8_t* punct;    /* device [N]: 1 = symbol not observed (uniform likelihood) */
@@ -141,6 +155,7 @@ typedef struct {
                                 no check at the same time; every column still sees the
                                 values of the sequential order, so results are the
                                 same bit for bit.  Ignored elsewhere. */
+    int32_t sus_kernel;      /* gfbp_sus_kernel */
 } gfbp_options;
 
 /*

@@ -128,13 +128,56 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
         }
     }
 
-    // one device allocation: rowptr | colptr | ecol | erow | cedge | eh | gexp | glog | cinfo | cdep | cpred
-    constexpr int NA = 11;
+    // SUS level schedule and its pieces (whole columns of one level, at most
+    // kLevelPiece (column, slot) pairs each)
+    std::vector<int> lev(N, 0);
+    int nlevels = 0;
+    for (int j = 0; j < N; j++) {
+        int m = -1;
+        for (int k = colptr[j]; k < colptr[j + 1]; k++) {
+            const int i = erow[cedge[k]];
+            for (int e2 = rowptr[i]; e2 < rowptr[i + 1]; e2++)
+                if (ecol[e2] < j) m = std::max(m, lev[ecol[e2]]);
+        }
+        lev[j] = m + 1;
+        nlevels = std::max(nlevels, lev[j] + 1);
+    }
+    std::vector<int> lorder(N);
+    {
+        std::vector<int> cnt(nlevels + 1, 0);
+        for (int j = 0; j < N; j++) cnt[lev[j] + 1]++;
+        for (int l = 0; l < nlevels; l++) cnt[l + 1] += cnt[l];
+        for (int j = 0; j < N; j++) lorder[cnt[lev[j]]++] = j;
+    }
+    std::vector<int2> lpair;
+    std::vector<int> lpiece(1, 0);
+    lpair.reserve(E);
+    {
+        int cur = -1, in_piece = 0;
+        for (int j : lorder) {
+            const int d = colptr[j + 1] - colptr[j];
+            if (lev[j] != cur || in_piece + d > gfbp::kLevelPiece) {
+                if (in_piece) lpiece.push_back((int)lpair.size());
+                in_piece = 0;
+                cur = lev[j];
+            }
+            for (int k = 0; k < d; k++) lpair.push_back(make_int2(j, k));
+            in_piece += d;
+        }
+        if (in_piece) lpiece.push_back((int)lpair.size());
+    }
+    const int npieces = (int)lpiece.size() - 1;
+
+    // one device allocation: rowptr | colptr | ecol | erow | cedge | eh | gexp | glog | cinfo | cdep | cpred |
+    // lpair | lpiece
+    constexpr int NA = 13;
     size_t off[NA], total = 0;
-    const size_t sz[NA] = {sizeof(int) * (size_t)(M + 1), sizeof(int) * (size_t)(N + 1), sizeof(int) * (size_t)E,
+    const size_t sz[] = {sizeof(int) * (size_t)(M + 1), sizeof(int) * (size_t)(N + 1), sizeof(int) * (size_t)E,
                            sizeof(int) * (size_t)E,       sizeof(int) * (size_t)E,       (size_t)E,
                            512,                           256,                           sizeof(int4) * (size_t)E,
-                           (size_t)N,                     sizeof(int) * (size_t)N};
+                           (size_t)N,                     sizeof(int) * (size_t)N,       sizeof(int2) * (size_t)E,
+                           sizeof(int) * lpiece.size()};
+    static_assert(sizeof(sz) / sizeof(sz[0]) == NA, "one size per array");
     for (int k = 0; k < NA; k++) { off[k] = total; total += align256(sz[k] ? sz[k] : 1); }
     std::vector<uint8_t> host(total, 0);
     std::memcpy(host.data() + off[0], rowptr.data(), sz[0]);
@@ -150,6 +193,8 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     std::memcpy(host.data() + off[7], lg, 256);
     std::memcpy(host.data() + off[9], cdep.data(), sz[9]);
     std::memcpy(host.data() + off[10], cpred.data(), sz[10]);
+    if (E) std::memcpy(host.data() + off[11], lpair.data(), sz[11]);
+    std::memcpy(host.data() + off[12], lpiece.data(), sz[12]);
 
     gfbp_code* c = new (std::nothrow) gfbp_code();
     if (!c) { set_error("gfbp_code_create: out of host memory"); return GFBP_ENOMEM; }
@@ -181,6 +226,10 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     d.cinfo = reinterpret_cast<const int4*>(base + off[8]);
     d.cdep = base + off[9];
     d.cpred = reinterpret_cast<const int*>(base + off[10]);
+    d.nlevels = nlevels;
+    d.npieces = npieces;
+    d.lpair = reinterpret_cast<const int2*>(base + off[11]);
+    d.lpiece = reinterpret_cast<const int*>(base + off[12]);
     c->poly = poly;
     *out = c;
     return GFBP_OK;

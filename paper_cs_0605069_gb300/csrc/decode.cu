@@ -304,6 +304,11 @@ gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const flo
     }
     A.method = (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > 16)) ? kTransform : kDirect;
     A.width = opt ? opt->sus_width : 0;
+    A.sus_kernel = opt ? opt->sus_kernel : GFBP_SUS_AUTO;
+    if (A.sus_kernel < GFBP_SUS_AUTO || A.sus_kernel > GFBP_SUS_LEVELS) {
+        set_error("unknown sus_kernel");
+        return GFBP_EINVAL;
+    }
     if (A.width != 0 && A.width != 1 && A.width != 2 && A.width != 4 && A.width != 8) {
         set_error("sus_width must be 0, 1, 2, 4 or 8");
         return GFBP_EINVAL;

@@ -42,7 +42,15 @@ struct CodeDev {
     const int4* cinfo;   // [E] per column slot: {edge, row start, row degree | h << 8, row}
     const uint8_t* cdep; // [N] 1 when column j shares a check with column j-1
     const int* cpred;    // [N] last column k < j sharing a check with column j, -1 if none
+    // SUS level schedule: level(j) = 1 + the highest level of the earlier
+    // columns that share a check with j.  Columns of one level share no check;
+    // updating the levels in turn gives the sequential order's values.
+    int nlevels, npieces;
+    const int2* lpair;   // [E] (column, slot) pairs, by level, columns increasing
+    const int* lpiece;   // [npieces+1] pair offsets: whole columns of one level, <= kLevelPiece pairs
 };
+
+constexpr int kLevelPiece = 128;
 
 struct DecodeArgs {
     CodeDev c;
@@ -84,6 +92,7 @@ struct DecodeArgs {
     int* fstate;
     int round_iters;       // resumable decoding: iterations per launch
     int width;             // SUS team kernels: teams per frame (0 = automatic)
+    int sus_kernel;        // gfbp_sus_kernel
 };
 
 // ---------------------------------------------------------------- helpers
@@ -571,6 +580,8 @@ bool sus_team_eligible(const DecodeArgs& A);
 cudaError_t launch_sus_team(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus_wave(const DecodeArgs& A, int width, int num_sms, cudaStream_t s);
 int sus_auto_width(const DecodeArgs& A, int num_sms);
+bool sus_level_eligible(const DecodeArgs& A);
+cudaError_t launch_sus_level(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s);

@@ -1,0 +1,304 @@
+// SUS (Sec. 2, steps 1-4) by levels of the column order, with one thread per
+// (column, check) pair and whole q-vectors in registers (q <= 16).
+//
+// Column j reads the stored q of the columns that share a check with it and
+// writes its own; two columns that share no check touch disjoint data.  With
+// level(j) = 1 + the highest level of the earlier columns sharing a check with
+// j, the columns of one level share no check, every earlier neighbour of j
+// sits on a lower level and every later one on a higher level.  Updating the
+// levels in turn, the columns of a level at once, therefore gives every column
+// exactly the operands of the sequential order j = 0..N-1.  A random (3,6)
+// code with N = 1000 has about 27 levels of about 37 columns.
+//
+// A CTA decodes one frame.  Each level is cut (on the host) into pieces of
+// whole columns with at most kLevelPiece pairs; per piece:
+//   step 1  thread <-> pair (j, k): r_kj of the column's k-th check folded from
+//           the check's other stored vectors (direct XOR-convolutions, all q
+//           entries of the operands in registers: q^2 FMAs per convolution,
+//           no shared-memory traffic), relabelled and normalised into a
+//           shared row;
+//   step 2  after a barrier, thread <-> pair (j, k): q_kj from the column's
+//           other rows (and Q_j, the hard decision and the posterior on slot 0),
+//           stored relabelled into the edge slab.
+// The arithmetic (each sum's order, each product's order, the normalisation)
+// is the single-team kernel's operation for operation, so the two give the
+// same bits.
+#pragma once
+
+#include "sus_team.cuh"
+
+namespace gfbp {
+
+namespace {
+
+template <int Q>
+__device__ __forceinline__ void ldq(float (&x)[Q], const float* p) {
+#pragma unroll
+    for (int i = 0; i < Q; i += 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p + i);
+        x[i] = a.x; x[i + 1] = a.y; x[i + 2] = a.z; x[i + 3] = a.w;
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void ldgq(float (&x)[Q], const float* p) {
+#pragma unroll
+    for (int i = 0; i < Q; i += 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p + i));
+        x[i] = a.x; x[i + 1] = a.y; x[i + 2] = a.z; x[i + 3] = a.w;
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void stq(float* p, const float (&x)[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; i += 4) *reinterpret_cast<float4*>(p + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+}
+
+// U <- U (*) Y, (U (*) Y)[y] = sum_x U[x] Y[x XOR y]: partial p over x = 4p..4p+3
+// in increasing x (one FMA chain), partials added in increasing p.
+template <int Q>
+__device__ __forceinline__ void xconv_regs(float (&U)[Q], const float (&Y)[Q]) {
+    constexpr int NP = Q / 4;
+    float o[Q];
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+        float t[Q];
+#pragma unroll
+        for (int y = 0; y < Q; y++) t[y] = fmaf(U[4 * p], Y[(4 * p) ^ y], 0.f);
+#pragma unroll
+        for (int xl = 1; xl < 4; xl++) {
+            const int x = 4 * p + xl;
+#pragma unroll
+            for (int y = 0; y < Q; y++) t[y] = fmaf(U[x], Y[x ^ y], t[y]);
+        }
+#pragma unroll
+        for (int y = 0; y < Q; y++) o[y] = (p == 0) ? t[y] : o[y] + t[y];
+    }
+#pragma unroll
+    for (int y = 0; y < Q; y++) U[y] = o[y];
+}
+
+// Pairwise tree over the index bits, lowest bit first (the order of slot_sum).
+template <int Q>
+__device__ __forceinline__ float tree_sum(const float (&x)[Q]) {
+    float s[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) s[i] = x[i];
+#pragma unroll
+    for (int w = 1; w < Q; w <<= 1)
+#pragma unroll
+        for (int i = 0; i < Q; i += 2 * w) s[i] = s[i] + s[i + w];
+    return s[0];
+}
+
+template <int Q>
+__device__ __forceinline__ void normalise_regs(float (&x)[Q]) {
+    const float s = tree_sum<Q>(x);
+    if (s > 0.f && s <= 3.0e38f) {
+        const float r = 1.0f / s;
+#pragma unroll
+        for (int i = 0; i < Q; i++) x[i] *= r;
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; i++) x[i] = 1.0f / Q;
+    }
+}
+
+// Step 1 for local pair lp of the piece: r of check k of column j into row.
+template <int Q, int DC>
+__device__ __forceinline__ void level_check(const DecodeArgs& A, const float* slab, const uint8_t* zf, int2 pr,
+                                            const uint8_t* s_mul, float* row) {
+    const int j = pr.x, k = pr.y;
+    const int4 in = A.c.cinfo[A.c.colptr[j] + k];
+    const int own = in.x - in.y;
+    const int dc = in.z & 255;
+    const int h = (in.z >> 8) & 255;
+    const int z = zf ? (zf[in.w] & (Q - 1)) : 0;
+    const float* D = slab + (size_t)in.y * Q;
+    float U[Q];
+    if (dc > 1) {
+        ldq<Q>(U, D + (0 < own ? 0 : 1) * Q);
+        float Y[Q];
+        if (dc > 2) ldq<Q>(Y, D + (1 < own ? 1 : 2) * Q);
+#pragma unroll 1
+        for (int n = 1; n < dc - 1; n++) {
+            float Yn[Q];
+            const bool more = n + 1 < dc - 1;
+            if (more) ldq<Q>(Yn, D + (n + 1 < own ? n + 1 : n + 2) * Q);
+            xconv_regs<Q>(U, Y);
+            if (more) {
+#pragma unroll
+                for (int i = 0; i < Q; i++) Y[i] = Yn[i];
+            }
+        }
+    } else {
+        // a check of degree 1: the XOR-sum of no other edges is 0
+#pragma unroll
+        for (int i = 0; i < Q; i++) U[i] = i == 0 ? 1.f : 0.f;
+    }
+    // r_ij[a] = s[z XOR h a], normalised
+#pragma unroll
+    for (int i = 0; i < Q; i++) row[i] = U[i];
+    float R[Q];
+#pragma unroll
+    for (int a = 0; a < Q; a++) R[a] = row[(z ^ s_mul[h * Q + a]) & (Q - 1)];
+    normalise_regs<Q>(R);
+#pragma unroll
+    for (int a = 0; a < Q; a++) row[a] = R[a];
+}
+
+// Step 2 for local pair lp: q of (j, k) from the column's other rows, and for
+// slot 0 the posterior Q_j and the hard decision.
+template <int Q>
+__device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* slab, uint8_t* xh, int2 pr,
+                                          const float* rows0, const uint8_t* s_div, float* orow) {
+    const int j = pr.x, k = pr.y;
+    const int c0 = A.c.colptr[j];
+    const int d = A.c.colptr[j + 1] - c0;
+    const int4 in = A.c.cinfo[c0 + k];
+    const int h = (in.z >> 8) & 255;
+    const int N = A.c.N;
+    float p[Q];
+    ldgq<Q>(p, A.L + ((size_t)f * N + j) * Q);
+    int si = -1;
+    if (A.markov) {
+        si = A.src_index[j];
+        if (si >= 0) {
+            float P[Q];
+            ldq<Q>(P, A.P + ((size_t)f * A.K + si) * Q);
+#pragma unroll
+            for (int i = 0; i < Q; i++) p[i] *= P[i];
+            normalise_regs<Q>(p);
+        }
+    }
+    float other[Q], all[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) { other[i] = p[i]; all[i] = p[i]; }
+    const float* r0 = rows0 - (size_t)k * (Q + 1);   // row of the column's slot 0
+#pragma unroll 1
+    for (int k2 = 0; k2 < d; k2++) {
+        const float* r = r0 + (size_t)k2 * (Q + 1);
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const float v = r[i];
+            all[i] *= v;
+            if (k2 != k) other[i] *= v;
+        }
+    }
+    if (k == 0) {
+        normalise_regs<Q>(all);
+        int bi = 0;
+        float bv = all[0];
+#pragma unroll
+        for (int i = 1; i < Q; i++)
+            if (all[i] > bv) { bv = all[i]; bi = i; }
+        xh[j] = (uint8_t)bi;
+        if (A.post) stq<Q>(A.post + ((size_t)f * N + j) * Q, all);
+        if (si >= 0) stq<Q>(A.Qsrc + ((size_t)f * A.K + si) * Q, all);
+    }
+    normalise_regs<Q>(other);
+    if (A.step) stq<Q>(A.msg_io + ((size_t)f * A.c.E + in.x) * Q, other);
+    // stored form: qt[y] = q[h^-1 y]
+#pragma unroll
+    for (int i = 0; i < Q; i++) orow[i] = other[i];
+    float qt[Q];
+#pragma unroll
+    for (int y = 0; y < Q; y++) qt[y] = orow[s_div[h * Q + y]];
+    stq<Q>(slab + (size_t)in.x * Q, qt);
+}
+
+template <int Q, int DC, int T>
+__device__ __forceinline__ void sus_level_frame(const DecodeArgs& A, int f, const uint8_t* s_mul,
+                                                const uint8_t* s_div, float* s_row, float* s_orow) {
+    constexpr int RS = Q + 1;   // shared row stride (conflict-free column access)
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int M = A.c.M, N = A.c.N;
+    float* slab = A.msg + (size_t)f * A.c.E * Q;
+    const uint8_t* zf = A.syn ? A.syn + (size_t)f * M : nullptr;
+    uint8_t* xh = A.xhat + (size_t)f * N;
+    float* orow = s_orow + tid * RS;
+
+    int t0 = 0;   // iterations already done (resumable decoding)
+    if (A.fstate) {
+        const int st = A.fstate[f];
+        if (st >> 30) return;
+        t0 = st;
+    }
+    int t = t0 + 1, ok = 0;
+    bool fin = false;
+    for (;; t++) {
+#pragma unroll 1
+        for (int pc = 0; pc < A.c.npieces; pc++) {
+            const int pb = A.c.lpiece[pc];
+            const int n = A.c.lpiece[pc + 1] - pb;
+            for (int lp = tid; lp < n; lp += T)
+                level_check<Q, DC>(A, slab, zf, A.c.lpair[pb + lp], s_mul, s_row + lp * RS);
+            __syncthreads();
+            for (int lp = tid; lp < n; lp += T)
+                level_var<Q>(A, f, slab, xh, A.c.lpair[pb + lp], s_row + lp * RS, s_div, orow);
+            __syncthreads();
+        }
+        int bad = 0;
+        for (int i = tid; i < M; i += T) {
+            int s = 0;
+            const int e1 = A.c.rowptr[i + 1];
+            for (int e = A.c.rowptr[i]; e < e1; e++) s ^= s_mul[A.c.eh[e] * Q + xh[A.c.ecol[e]]];
+            bad |= (s != (zf ? (zf[i] & (Q - 1)) : 0));
+        }
+        ok = !__syncthreads_or(bad);
+        if (A.trace) {
+            uint8_t* tr = A.trace + ((size_t)f * A.max_iter + (t - 1)) * N;
+            for (int jj = tid; jj < N; jj += T) tr[jj] = xh[jj];
+        }
+        if ((ok && A.early_stop) || t >= A.max_iter) {
+            fin = true;
+            break;
+        }
+        if (A.markov) {
+            for (int i = warp; i < A.K; i += T / 32)
+                team_prior<Q, 32>(A, f, i, A.P + ((size_t)f * A.K + i) * Q, 0xffffffffu, lane);
+            __syncthreads();
+        }
+        if (A.fstate && t - t0 >= A.round_iters) break;
+    }
+    if (A.step && A.markov && A.prior_out) {
+        for (int i = warp; i < A.K; i += T / 32)
+            team_prior<Q, 32>(A, f, i, A.prior_out + ((size_t)f * A.K + i) * Q, 0xffffffffu, lane);
+    }
+    if (A.trace) {
+        for (size_t o = (size_t)t * N + tid; o < (size_t)A.max_iter * N; o += T)
+            A.trace[(size_t)f * A.max_iter * N + o] = 255;
+    }
+    if (tid == 0) {
+        if (!A.fstate || fin) {
+            if (A.iters) A.iters[f] = t;
+            A.conv[f] = (uint8_t)ok;
+        }
+        if (A.fstate) A.fstate[f] = fin ? (t | (1 << 30)) : t;
+    }
+}
+
+template <int Q, int DC, int T>
+__global__ void __launch_bounds__(T) k_sus_level(const DecodeArgs A) {
+    static_assert(T % 32 == 0, "whole warps");
+    __shared__ uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a
+    __shared__ uint8_t s_div[Q * Q];   // s_div[h*Q + b] = h^-1 b
+    __shared__ float s_row[kLevelPiece * (Q + 1)];
+    __shared__ float s_orow[T * (Q + 1)];
+    __shared__ int s_f;
+    const int tid = threadIdx.x;
+    team_tables<Q>(A.c.gexp, A.c.glog, s_mul, s_div, tid, T);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_f = atomicAdd(A.work, 1);
+        __syncthreads();
+        const int f = s_f;
+        if (f >= A.F) break;
+        sus_level_frame<Q, DC, T>(A, f, s_mul, s_div, s_row, s_orow);
+    }
+}
+
+}  // namespace
+}  // namespace gfbp

@@ -23,12 +23,19 @@ namespace {
 constexpr int kTeamThreads = 128;
 constexpr int kSlots = 4;
 
-template <int Q>
+// Lanes per slot vector (GS), entries per lane (V) and lanes per team; both
+// team kernels use GS = min(q, 8).  Every sum below runs in an order fixed by
+// the entry indices alone, so any GS gives the same bits.  (GS = q / 4, four
+// entries per lane with 128-bit shared loads, needs fewer instructions per
+// column but puts two teams in a warp whose waits diverge, and ran 1.7x
+// slower on the GF(16) N = 1000 batch.)
+template <int Q, int GS_ = (Q < 8 ? Q : 8)>
 struct TeamLay {
-    static constexpr int GS = Q < 8 ? Q : 8;       // lanes per vector
-    static constexpr int V = Q / GS;                 // entries per lane
-    static constexpr int TEAM = kSlots * GS;         // lanes per frame
-    static_assert(TEAM == 16 || TEAM == 32 || TEAM == 8, "team must divide a warp");
+    static constexpr int GS = GS_;
+    static constexpr int V = Q / GS;
+    static constexpr int TEAM = kSlots * GS;
+    static_assert(V * GS == Q && V <= 4, "at most four entries per lane");
+    static_assert(TEAM == 4 || TEAM == 8 || TEAM == 16 || TEAM == 32, "team must divide a warp");
 };
 
 template <int L>
@@ -42,10 +49,11 @@ __device__ __forceinline__ unsigned lanes_mask() {
 }
 
 // out[v] = sum_x sa[x] sb[x XOR y] for y = g*V + v (whole vectors in shared memory).
-// Four partial sums per output keep the dependent FMA chain short.
+// Partial sum p takes x = 4p .. 4p+3 in increasing order (one FMA chain each),
+// and the partials are added in increasing p: the same order for any V <= 4.
 template <int Q, int V>
 __device__ __forceinline__ void xconv_team(float (&out)[V], const float* sa, const float* sb, int g) {
-    constexpr int NP = (Q / V) < 4 ? (Q / V) : 4;
+    constexpr int NP = Q / 4 > 0 ? Q / 4 : 1;
     float acc[NP][V];
 #pragma unroll
     for (int p = 0; p < NP; p++)
@@ -56,7 +64,7 @@ __device__ __forceinline__ void xconv_team(float (&out)[V], const float* sa, con
         float a[V], b[V];
         ldv<V>(a, sa + xb);
         ldv<V>(b, sb + (xb ^ (g * V)));
-        const int p = (xb / V) % NP;
+        const int p = xb / 4;
 #pragma unroll
         for (int xl = 0; xl < V; xl++) {
 #pragma unroll
@@ -72,11 +80,14 @@ __device__ __forceinline__ void xconv_team(float (&out)[V], const float* sa, con
     }
 }
 
+// Sum of the slot's q entries as a pairwise tree over the index bits, lowest
+// bit first (inside the lane, then across lanes): the same bits for any GS.
 template <int GS, int V>
 __device__ __forceinline__ float slot_sum(const float (&x)[V], unsigned smask) {
-    float s = 0.f;
-#pragma unroll
-    for (int v = 0; v < V; v++) s += x[v];
+    float s;
+    if constexpr (V == 4) s = (x[0] + x[1]) + (x[2] + x[3]);
+    else if constexpr (V == 2) s = x[0] + x[1];
+    else s = x[0];
 #pragma unroll
     for (int m = 1; m < GS; m <<= 1) s += __shfl_xor_sync(smask, s, m);
     return s;
@@ -111,19 +122,18 @@ __device__ __forceinline__ int slot_argmax(const float (&x)[V], unsigned smask, 
     return bi;
 }
 
-template <int Q, int DC>
+template <int Q, int DC, int V>
 struct SlotBuf {
-    float D[DC][TeamLay<Q>::V];
-    float L[TeamLay<Q>::V];  // channel likelihood of the column's symbol
+    float D[DC][V];
+    float L[V];              // channel likelihood of the column's symbol
     int4 info;               // {edge, row start, row degree | h << 8, row}
     int d;                   // column degree
     int dep;                 // column shares a check with the previous one
 };
 
-template <int Q, int DC>
-__device__ __forceinline__ void slot_load(SlotBuf<Q, DC>& b, const DecodeArgs& A, const float* slab, int f, int j,
+template <int Q, int DC, int V>
+__device__ __forceinline__ void slot_load(SlotBuf<Q, DC, V>& b, const DecodeArgs& A, const float* slab, int f, int j,
                                           int k, int g) {
-    constexpr int V = TeamLay<Q>::V;
     const int c0 = A.c.colptr[j];
     b.d = A.c.colptr[j + 1] - c0;
     b.dep = A.c.cdep[j];
@@ -165,11 +175,11 @@ __device__ __forceinline__ void team_prior(const DecodeArgs& A, int f, int i, fl
 // `cur`, then Q_j (hard decision, posterior, Markov source posterior) and the
 // new stored q_ij.  s_mul / s_div: the field's multiply and divide-by-h
 // tables; sa: this slot's shared scratch (2q + 4 floats).
-template <int Q, int DC>
-__device__ __forceinline__ void team_column(const DecodeArgs& A, int f, int j, const SlotBuf<Q, DC>& cur,
+template <int Q, int DC, int GS_>
+__device__ __forceinline__ void team_column(const DecodeArgs& A, int f, int j, const SlotBuf<Q, DC, Q / GS_>& cur,
                                             const uint8_t* s_mul, const uint8_t* s_div, float* sa, float* slab,
                                             const uint8_t* zf, uint8_t* xh) {
-    using TL = TeamLay<Q>;
+    using TL = TeamLay<Q, GS_>;
     constexpr int GS = TL::GS, V = TL::V, TEAM = TL::TEAM;
     const int tl = threadIdx.x & (TEAM - 1);
     const int k = tl / GS;
@@ -275,7 +285,7 @@ template <int Q, int DC>
 __device__ __forceinline__ void sus_team_frame(const DecodeArgs& A, int f, const uint8_t* s_mul,
                                                const uint8_t* s_div, float* sa) {
     using TL = TeamLay<Q>;
-    constexpr int GS = TL::GS, TEAM = TL::TEAM;
+    constexpr int GS = TL::GS, V = TL::V, TEAM = TL::TEAM;
     const int tl = threadIdx.x & (TEAM - 1);
     const int k = tl / GS;
     const int g = tl & (GS - 1);
@@ -295,13 +305,13 @@ __device__ __forceinline__ void sus_team_frame(const DecodeArgs& A, int f, const
     int t = t0 + 1, ok = 0;
     bool fin = false;
     for (;; t++) {
-        SlotBuf<Q, DC> cur, nxt;
-        slot_load<Q, DC>(cur, A, slab, f, 0, k, g);
+        SlotBuf<Q, DC, V> cur, nxt;
+        slot_load<Q, DC, V>(cur, A, slab, f, 0, k, g);
         for (int j = 0; j < N; j++) {
-            if (j + 1 < N) slot_load<Q, DC>(nxt, A, slab, f, j + 1, k, g);
-            team_column<Q, DC>(A, f, j, cur, s_mul, s_div, sa, slab, zf, xh);
+            if (j + 1 < N) slot_load<Q, DC, V>(nxt, A, slab, f, j + 1, k, g);
+            team_column<Q, DC, GS>(A, f, j, cur, s_mul, s_div, sa, slab, zf, xh);
             if (j + 1 < N) {
-                if (nxt.dep) slot_load<Q, DC>(nxt, A, slab, f, j + 1, k, g);
+                if (nxt.dep) slot_load<Q, DC, V>(nxt, A, slab, f, j + 1, k, g);
                 cur = nxt;
             }
         }

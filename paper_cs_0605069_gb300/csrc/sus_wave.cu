@@ -7,7 +7,7 @@ namespace {
 
 template <int Q, int DC, int W>
 cudaError_t launch_wave_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
-    constexpr int threads = W * TeamLay<Q>::TEAM;
+    constexpr int threads = W * WaveLay<Q>::TEAM;
     static int occ = -1;
     if (occ < 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_wave<Q, DC, W>, threads, 0);

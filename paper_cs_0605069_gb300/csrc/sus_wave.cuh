@@ -55,12 +55,16 @@ __device__ __forceinline__ bool wave_wait(const volatile int* prog, int p) {
     return false;
 }
 
+// Lanes per slot of the multi-team kernel (one team per warp for q >= 8).
+template <int Q>
+using WaveLay = TeamLay<Q>;
+
 // One frame's whole SUS decode by the W teams of the calling CTA.
 template <int Q, int DC, int W>
 __device__ __forceinline__ void sus_wave_frame(const DecodeArgs& A, int f, const uint8_t* s_mul,
                                                const uint8_t* s_div, float* sa, volatile int* prog, int* s_fail) {
-    using TL = TeamLay<Q>;
-    constexpr int GS = TL::GS, TEAM = TL::TEAM, NTH = W * TEAM;
+    using TL = WaveLay<Q>;
+    constexpr int GS = TL::GS, V = TL::V, TEAM = TL::TEAM, NTH = W * TEAM;
     const int tid = threadIdx.x;
     const int w = tid / TEAM;
     const int tl = tid & (TEAM - 1);
@@ -88,11 +92,11 @@ __device__ __forceinline__ void sus_wave_frame(const DecodeArgs& A, int f, const
         int fail = 0;
         int jc = w;
         if (jc < N) {
-            SlotBuf<Q, DC> cur, nxt;
+            SlotBuf<Q, DC, V> cur, nxt;
             int pc = A.c.cpred[jc];
             int wmc = wave_watermark<W>(prog);
             __threadfence_block();
-            slot_load<Q, DC>(cur, A, slab, f, jc, k, g);
+            slot_load<Q, DC, V>(cur, A, slab, f, jc, k, g);
             for (;;) {
                 const int jn = jc + W;
                 int pn = 0, wmn = 0;
@@ -100,13 +104,13 @@ __device__ __forceinline__ void sus_wave_frame(const DecodeArgs& A, int f, const
                     pn = A.c.cpred[jn];
                     wmn = wave_watermark<W>(prog);
                     __threadfence_block();
-                    slot_load<Q, DC>(nxt, A, slab, f, jn, k, g);
+                    slot_load<Q, DC, V>(nxt, A, slab, f, jn, k, g);
                 }
                 if (wmc <= pc) {
                     if (!wave_wait<W>(prog, pc)) fail = 1;
-                    slot_load<Q, DC>(cur, A, slab, f, jc, k, g);
+                    slot_load<Q, DC, V>(cur, A, slab, f, jc, k, g);
                 }
-                team_column<Q, DC>(A, f, jc, cur, s_mul, s_div, sa, slab, zf, xh);
+                team_column<Q, DC, GS>(A, f, jc, cur, s_mul, s_div, sa, slab, zf, xh);
                 __threadfence_block();
                 __syncwarp(tmask);
                 if (tl == 0) prog[w] = jn;
@@ -160,8 +164,8 @@ __device__ __forceinline__ void sus_wave_frame(const DecodeArgs& A, int f, const
 }
 
 template <int Q, int DC, int W>
-__global__ void __launch_bounds__(W * TeamLay<Q>::TEAM) k_sus_wave(const DecodeArgs A) {
-    using TL = TeamLay<Q>;
+__global__ void __launch_bounds__(W * WaveLay<Q>::TEAM) k_sus_wave(const DecodeArgs A) {
+    using TL = WaveLay<Q>;
     constexpr int GS = TL::GS, NTH = W * TL::TEAM;
     constexpr int SCR = 2 * Q + 4;   // per slot: two operand vectors (+ bank padding)
     __shared__ uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a

@@ -18,7 +18,8 @@ def to_dev(a, dtype=None):
 
 
 def gpu_decode(code_dev, obs, channel, param, schedule, max_iter, T=None, K=0, src_pos=None, punct=None,
-               syndrome=None, trace=False, post=False, no_early_stop=False, check_method="auto", sus_width=0):
+               syndrome=None, trace=False, post=False, no_early_stop=False, check_method="auto", sus_width=0,
+               sus_kernel="auto"):
     import torch
     from paper_cs_0605069_gb300 import gfbp
     fp = np.asarray(param, np.float32)
@@ -27,7 +28,8 @@ def gpu_decode(code_dev, obs, channel, param, schedule, max_iter, T=None, K=0, s
                       schedule=schedule, max_iter=max_iter, T=T, K=K, src_pos=src_pos, frame_param=frame_param,
                       punct=None if punct is None else to_dev(punct),
                       syndrome=None if syndrome is None else to_dev(syndrome), post=post, trace=trace,
-                      no_early_stop=no_early_stop, check_method=check_method, sus_width=sus_width)
+                      no_early_stop=no_early_stop, check_method=check_method, sus_width=sus_width,
+                      sus_kernel=sus_kernel)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
 

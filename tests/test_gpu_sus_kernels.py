@@ -1,10 +1,11 @@
-"""SUS with several lane teams per frame against one team per frame.
+"""The SUS kernels that reorder work against one lane team per frame.
 
-The multi-team kernel runs columns that share no check at the same time and
-starts a column only after the last earlier column sharing a check with it has
-finished, so every column reads the values of the strictly sequential order:
-its results must equal the single-team kernel's bit for bit (x_hat, iters,
-converged, posteriors, traces, lock-step messages)."""
+The multi-team kernel starts a column once the last earlier column sharing a
+check with it has finished; the level kernel updates the columns level by level
+(one level's columns share no check).  Both give every column the operands of
+the strictly sequential order with the single-team kernel's arithmetic, so
+their results must equal its results bit for bit (x_hat, iters, converged,
+posteriors, traces, lock-step messages)."""
 import numpy as np
 import pytest
 
@@ -31,11 +32,15 @@ def _same(a, b, what):
         assert np.array_equal(x, y), f"{what}: {k} differs"
 
 
-def _widths(cd, obs, kind, param, max_iter, widths=(2, 4, 8), **kw):
-    ref = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, sus_width=1, **kw)
-    for w in widths:
-        out = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, sus_width=w, **kw)
-        _same(ref, out, f"width {w}")
+def _widths(cd, obs, kind, param, max_iter, widths=(2, 4, 8), levels=True, **kw):
+    ref = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, sus_kernel="teams", sus_width=1,
+                     **kw)
+    runs = [(f"width {w}", dict(sus_kernel="teams", sus_width=w)) for w in widths]
+    if levels:
+        runs.append(("levels", dict(sus_kernel="levels")))
+    for what, v in runs:
+        out = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, **v, **kw)
+        _same(ref, out, what)
     return ref
 
 
@@ -99,13 +104,38 @@ def test_wave_lockstep_step_equals_single_team(torch_cuda, oracle):
     prior = to_dev(np.broadcast_to(pi, (F, b.K, b.code.q)).astype(np.float32).copy())
     fp = to_dev(np.asarray(b.param, np.float32))
     outs = {}
-    for w in (1, 4):
+    for name, v in (("one team", dict(sus_kernel="teams", sus_width=1)), ("width 4", dict(sus_kernel="teams",
+                    sus_width=4)), ("levels", dict(sus_kernel="levels"))):
         m = to_dev(msg0.astype(np.float32))
         o = gfbp.step(cd, to_dev(b.obs, torch.float32), m, channel=b.channel, schedule="sus", T=b.T, K=b.K,
-                      prior_in=prior, frame_param=fp, sus_width=w)
+                      prior_in=prior, frame_param=fp, **v)
         torch.cuda.synchronize()
-        outs[w] = {k: v.cpu().numpy() for k, v in o.items() if v is not None}
-    _same(outs[1], outs[4], "step width 4")
+        outs[name] = {k: x.cpu().numpy() for k, x in o.items() if x is not None}
+    _same(outs["one team"], outs["width 4"], "step width 4")
+    _same(outs["one team"], outs["levels"], "step levels")
+
+
+def test_levels_column_degree_above_team_limit(torch_cuda, oracle):
+    """Column degree 6 (beyond the team kernels): the level kernel against the
+    oracle in lock-step (one SUS iteration from the same messages)."""
+    import torch
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    from tests.parity_util import LOCKSTEP_ATOL
+    code = W.regular_code(8, 120, dv=6, dc=12, cfg="levels_dv6", encodable=False)
+    rng = np.random.default_rng(11)
+    F = 6
+    obs = W.bsc(rng, np.zeros((F, code.N), np.int64), code.p, 0.03)
+    cd = gfbp.Code.from_coo(code)
+    fp = to_dev(np.full(F, 0.03, np.float32))
+    msg = oracle.initial_messages(code, obs, "bsc", 0.03)
+    for it in range(3):
+        ref = oracle.step(code, obs, "bsc", 0.03, msg, "sus")
+        o = gfbp.step(cd, to_dev(obs, torch.float32), to_dev(msg.astype(np.float32)), channel="bsc",
+                      schedule="sus", frame_param=fp, sus_kernel="levels")
+        torch.cuda.synchronize()
+        assert np.abs(o["post"].cpu().numpy() - ref["post"]).max() <= LOCKSTEP_ATOL
+        assert np.abs(o["msg"].cpu().numpy() - ref["msg"]).max() <= LOCKSTEP_ATOL
+        msg = ref["msg"]
 
 
 def test_wave_width_is_validated(torch_cuda):
@@ -115,3 +145,6 @@ def test_wave_width_is_validated(torch_cuda):
     cd = gfbp.Code.from_coo(b.code)
     with pytest.raises(gfbp.GfbpError):
         gfbp.decode(cd, to_dev(b.obs, torch.float32), b.channel, float(b.param[0]), schedule="sus", sus_width=3)
+    with pytest.raises(KeyError):
+        gfbp.decode(cd, to_dev(b.obs, torch.float32), b.channel, float(b.param[0]), schedule="sus",
+                    sus_kernel="fastest")
