@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--method", default="auto", choices=["auto", "direct", "transform"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sus-width", type=int, default=0, help="SUS lane teams per frame (0 = automatic)")
-    ap.add_argument("--sus-kernel", default="auto", choices=["auto", "teams", "levels"])
+    ap.add_argument("--layout", default="auto", choices=["auto", "lanes", "thread"])
     ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve"],
                     help="batch: the GF(16) N=1000 benchmark (default); mixed: frames of 12 (q, N) classes in one "
                          "persistent launch; serve: Poisson arrivals to the continuous-batching server")
@@ -232,7 +232,7 @@ def main():
             ev = record[s] if record else None
             gfbp.decode(code, obs, "awgn", 0.0, schedule=s, max_iter=max_iter, frame_param=sig,
                         workspace=ws[s], out=outs[s], kernel_events=ev, check_method=args.method,
-                        sus_width=args.sus_width, sus_kernel=args.sus_kernel)
+                        sus_width=args.sus_width, layout=args.layout)
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -285,7 +285,7 @@ def main():
             for s in scheds:
                 gfbp.decode(code, obs_d, "awgn", 0.0, schedule=s, max_iter=max_iter, frame_param=sig_d,
                             workspace=ws[s], out=outs[s], check_method=args.method, sus_width=args.sus_width,
-                            sus_kernel=args.sus_kernel)
+                            layout=args.layout)
                 for k in outs[s]:
                     host_out[s][k].copy_(outs[s][k], non_blocking=True)
 
@@ -340,7 +340,7 @@ def main():
             "config": {"workload": WORKLOAD, "q": q, "N": N, "M": b.code.M, "code": "regular (3,6) rate 1/2",
                        "channel": "BI-AWGN, Eb/N0 1.0/1.5/2.0 dB round-robin", "frames_per_gpu": F,
                        "max_iter": max_iter, "schedules": list(scheds), "check_method": args.method,
-                       "sus_kernel": args.sus_kernel, "sus_width": args.sus_width,
+                       "layout": args.layout, "sus_width": args.sus_width,
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"frames sharded over {world} GPU(s), no collective"},
             "sym_iter_per_s": sum(per[s]["sym_iter_per_s"] for s in scheds) / len(scheds),

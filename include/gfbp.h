@@ -122,18 +122,22 @@ typedef struct {
 typedef enum { GFBP_CHECK_AUTO = 0, GFBP_CHECK_TRANSFORM = 1, GFBP_CHECK_DIRECT = 2 } gfbp_check_method;
 
 /*
- * SUS kernel for q = 4, 8, 16 with the DIRECT check node.  Both give the
- * values of the sequential column order j = 0..N-1, bit for bit:
- *   TEAMS   lane teams walk the columns in order; with sus_width > 1 teams a
- *           column starts once the last earlier column sharing a check with
- *           it is done (column degree <= 4, row degree <= 8).
- *   LEVELS  the columns are grouped into levels (level(j) = 1 + the highest
- *           level of the earlier columns sharing a check with j; one level's
- *           columns share no check) and a level's (column, check) pairs run
- *           at once, one thread each.
- *   AUTO    LEVELS where it applies, else TEAMS.
+ * How the kernels for q = 4, 8, 16 with the DIRECT check node hold a
+ * q-vector.  Both layouts give the same bits.
+ *   LANES   spread over a group of lanes.  PUS: a lane group per check and
+ *           per column.  SUS: lane teams walk the columns in order; with
+ *           sus_width > 1 teams per frame, a column starts once the last
+ *           earlier column sharing a check with it is done (column degree
+ *           <= 4, row degree <= 8).
+ *   THREAD  in one thread's registers.  PUS: a thread per check and per
+ *           column.  SUS: the columns are grouped into levels (level(j) = 1 +
+ *           the highest level of the earlier columns sharing a check with j;
+ *           one level's columns share no check) and a level's (column, check)
+ *           pairs run at once, a thread each.
+ *   AUTO    THREAD for SUS, LANES for PUS (the faster of the two on the
+ *           GF(16) N = 1000 benchmark batch).
  */
-typedef enum { GFBP_SUS_AUTO = 0, GFBP_SUS_TEAMS = 1, GFBP_SUS_LEVELS = 2 } gfbp_sus_kernel;
+typedef enum { GFBP_LAYOUT_AUTO = 0, GFBP_LAYOUT_LANES = 1, GFBP_LAYOUT_THREAD = 2 } gfbp_layout;
 
 /* Optional inputs and outputs of gfbp_decode / gfbp_step (NULL = defaults). */
 typedef struct {
@@ -149,13 +153,12 @@ typedef struct {
     void* kernel_events[2];  /* optional cudaEvent_t pair, recorded on `stream` right before
                                 and right after the schedule kernel (for timing it alone) */
     int32_t check_method;    /* gfbp_check_method for the horizontal pass (Eq. 3) */
-    int32_t sus_width;       /* SUS with q <= 16, column degree <= 4, row degree <= 8:
-                                lane teams per frame, 1, 2, 4 or 8 (0 = chosen from
-                                the frame count).  Teams > 1 update columns that share
-                                no check at the same time; every column still sees the
-                                values of the sequential order, so results are the
-                                same bit for bit.  Ignored elsewhere. */
-    int32_t sus_kernel;      /* gfbp_sus_kernel */
+    int32_t sus_width;       /* SUS, LANES layout: lane teams per frame, 1, 2, 4 or 8
+                                (0 = chosen from the frame count).  Teams > 1 update
+                                columns that share no check at the same time; every
+                                column still sees the values of the sequential order,
+                                so results are the same bit for bit. */
+    int32_t layout;          /* gfbp_layout */
 } gfbp_options;
 
 /*

@@ -304,9 +304,9 @@ gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const flo
     }
     A.method = (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > 16)) ? kTransform : kDirect;
     A.width = opt ? opt->sus_width : 0;
-    A.sus_kernel = opt ? opt->sus_kernel : GFBP_SUS_AUTO;
-    if (A.sus_kernel < GFBP_SUS_AUTO || A.sus_kernel > GFBP_SUS_LEVELS) {
-        set_error("unknown sus_kernel");
+    A.layout = opt ? opt->layout : GFBP_LAYOUT_AUTO;
+    if (A.layout < GFBP_LAYOUT_AUTO || A.layout > GFBP_LAYOUT_THREAD) {
+        set_error("unknown layout");
         return GFBP_EINVAL;
     }
     if (A.width != 0 && A.width != 1 && A.width != 2 && A.width != 4 && A.width != 8) {

@@ -92,7 +92,7 @@ struct DecodeArgs {
     int* fstate;
     int round_iters;       // resumable decoding: iterations per launch
     int width;             // SUS team kernels: teams per frame (0 = automatic)
-    int sus_kernel;        // gfbp_sus_kernel
+    int layout;            // gfbp_layout
 };
 
 // ---------------------------------------------------------------- helpers
@@ -581,6 +581,7 @@ cudaError_t launch_sus_team(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus_wave(const DecodeArgs& A, int width, int num_sms, cudaStream_t s);
 int sus_auto_width(const DecodeArgs& A, int num_sms);
 bool sus_level_eligible(const DecodeArgs& A);
+bool pus_regs_eligible(const DecodeArgs& A);
 cudaError_t launch_sus_level(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);

@@ -1,5 +1,5 @@
-// Launchers of the PUS kernel (device code in pus_frame.cuh).
-#include "pus_frame.cuh"
+// Launchers of the PUS kernels (device code in pus_frame.cuh and pus_regs.cuh).
+#include "pus_regs.cuh"
 
 namespace gfbp {
 
@@ -39,9 +39,48 @@ cudaError_t launch_method(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     return launch_deg<Q, kTransform>(A, num_sms, s);
 }
 
+constexpr int kPusRegsThreads = 128;
+
+template <int Q>
+cudaError_t launch_regs_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    constexpr int T = kPusRegsThreads;
+    const size_t smem = sizeof(float) * (size_t)(pus_regs_rows(A.c.dcmax, A.c.dvmax) + 1) * T * (Q + 1);
+    static size_t smem_set = 0;   // largest dynamic size enabled so far
+    static int occ_smem = -1;
+    static int occ = 1;
+    cudaError_t e = cudaSuccess;
+    if (smem > smem_set) {
+        e = cudaFuncSetAttribute(k_pus_regs<Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    if ((int)smem != occ_smem) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus_regs<Q, T>, T, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+        occ_smem = (int)smem;
+    }
+    long long grid = (long long)num_sms * occ;
+    if (grid > A.F) grid = A.F;
+    if (grid < 1) return cudaSuccess;
+    k_pus_regs<Q, T><<<(int)grid, T, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
+bool pus_regs_eligible(const DecodeArgs& A) {
+    return A.method == kDirect && A.c.q >= 4 && A.c.q <= 16;
+}
+
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    if (A.layout == GFBP_LAYOUT_THREAD && pus_regs_eligible(A)) {
+        switch (A.c.q) {
+        case 4: return launch_regs_q<4>(A, num_sms, s);
+        case 8: return launch_regs_q<8>(A, num_sms, s);
+        case 16: return launch_regs_q<16>(A, num_sms, s);
+        }
+    }
     switch (A.c.q) {
     case 2: return launch_method<2>(A, num_sms, s);
     case 4: return launch_method<4>(A, num_sms, s);

@@ -49,6 +49,13 @@ __device__ __forceinline__ void ldgq(float (&x)[Q], const float* p) {
     }
 }
 
+// Non-binding L1 prefetch of the 128-byte lines covering [p, p + bytes).
+__device__ __forceinline__ void prefetch_l1(const void* p, int bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)127;
+    const uintptr_t e = reinterpret_cast<uintptr_t>(p) + (uintptr_t)bytes;
+    for (uintptr_t l = a; l < e; l += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(l));
+}
+
 template <int Q>
 __device__ __forceinline__ void stq(float* p, const float (&x)[Q]) {
 #pragma unroll
@@ -107,8 +114,8 @@ __device__ __forceinline__ void normalise_regs(float (&x)[Q]) {
 
 // Step 1 for local pair lp of the piece: r of check k of column j into row.
 template <int Q, int DC>
-__device__ __forceinline__ void level_check(const DecodeArgs& A, const float* slab, const uint8_t* zf, int2 pr,
-                                            const uint8_t* s_mul, float* row) {
+__device__ __forceinline__ void level_check(const DecodeArgs& A, int f, const float* slab, const uint8_t* zf,
+                                            int2 pr, const uint8_t* s_mul, float* row) {
     const int j = pr.x, k = pr.y;
     const int4 in = A.c.cinfo[A.c.colptr[j] + k];
     const int own = in.x - in.y;
@@ -116,6 +123,10 @@ __device__ __forceinline__ void level_check(const DecodeArgs& A, const float* sl
     const int h = (in.z >> 8) & 255;
     const int z = zf ? (zf[in.w] & (Q - 1)) : 0;
     const float* D = slab + (size_t)in.y * Q;
+    // the check's vectors are contiguous: bring them all towards L1 at once, so
+    // that the fold below waits for memory about once
+    prefetch_l1(D, dc * Q * (int)sizeof(float));
+    if (k == 0) prefetch_l1(A.L + ((size_t)f * A.c.N + j) * Q, Q * (int)sizeof(float));   // for step 2
     float U[Q];
     if (dc > 1) {
         ldq<Q>(U, D + (0 < own ? 0 : 1) * Q);
@@ -123,7 +134,7 @@ __device__ __forceinline__ void level_check(const DecodeArgs& A, const float* sl
         if (dc > 2) ldq<Q>(Y, D + (1 < own ? 1 : 2) * Q);
 #pragma unroll 1
         for (int n = 1; n < dc - 1; n++) {
-            float Yn[Q];
+            float Yn[Q];   // next operand, loaded one convolution ahead
             const bool more = n + 1 < dc - 1;
             if (more) ldq<Q>(Yn, D + (n + 1 < own ? n + 1 : n + 2) * Q);
             xconv_regs<Q>(U, Y);
@@ -234,7 +245,7 @@ __device__ __forceinline__ void sus_level_frame(const DecodeArgs& A, int f, cons
             const int pb = A.c.lpiece[pc];
             const int n = A.c.lpiece[pc + 1] - pb;
             for (int lp = tid; lp < n; lp += T)
-                level_check<Q, DC>(A, slab, zf, A.c.lpair[pb + lp], s_mul, s_row + lp * RS);
+                level_check<Q, DC>(A, f, slab, zf, A.c.lpair[pb + lp], s_mul, s_row + lp * RS);
             __syncthreads();
             for (int lp = tid; lp < n; lp += T)
                 level_var<Q>(A, f, slab, xh, A.c.lpair[pb + lp], s_row + lp * RS, s_div, orow);
@@ -281,7 +292,7 @@ __device__ __forceinline__ void sus_level_frame(const DecodeArgs& A, int f, cons
 }
 
 template <int Q, int DC, int T>
-__global__ void __launch_bounds__(T) k_sus_level(const DecodeArgs A) {
+__global__ void __launch_bounds__(T, 640 / T) k_sus_level(const DecodeArgs A) {
     static_assert(T % 32 == 0, "whole warps");
     __shared__ uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a
     __shared__ uint8_t s_div[Q * Q];   // s_div[h*Q + b] = h^-1 b

@@ -1,11 +1,13 @@
-"""The SUS kernels that reorder work against one lane team per frame.
+"""Kernels that hold or order the work differently must give the same bits.
 
-The multi-team kernel starts a column once the last earlier column sharing a
-check with it has finished; the level kernel updates the columns level by level
-(one level's columns share no check).  Both give every column the operands of
-the strictly sequential order with the single-team kernel's arithmetic, so
-their results must equal its results bit for bit (x_hat, iters, converged,
-posteriors, traces, lock-step messages)."""
+SUS: the multi-team kernel starts a column once the last earlier column sharing
+a check with it has finished; the level kernel (thread layout) updates the
+columns level by level (one level's columns share no check).  Both give every
+column the operands of the strictly sequential order with the single-team
+kernel's arithmetic.  PUS: the thread layout (a check or a column per thread,
+vectors in registers) runs the lane-group kernel's arithmetic in the same
+order.  So x_hat, iters, converged, posteriors, traces and lock-step messages
+must match the lane kernels bit for bit."""
 import numpy as np
 import pytest
 
@@ -33,11 +35,11 @@ def _same(a, b, what):
 
 
 def _widths(cd, obs, kind, param, max_iter, widths=(2, 4, 8), levels=True, **kw):
-    ref = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, sus_kernel="teams", sus_width=1,
+    ref = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, layout="lanes", sus_width=1,
                      **kw)
-    runs = [(f"width {w}", dict(sus_kernel="teams", sus_width=w)) for w in widths]
+    runs = [(f"width {w}", dict(layout="lanes", sus_width=w)) for w in widths]
     if levels:
-        runs.append(("levels", dict(sus_kernel="levels")))
+        runs.append(("levels", dict(layout="thread")))
     for what, v in runs:
         out = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, **v, **kw)
         _same(ref, out, what)
@@ -104,8 +106,8 @@ def test_wave_lockstep_step_equals_single_team(torch_cuda, oracle):
     prior = to_dev(np.broadcast_to(pi, (F, b.K, b.code.q)).astype(np.float32).copy())
     fp = to_dev(np.asarray(b.param, np.float32))
     outs = {}
-    for name, v in (("one team", dict(sus_kernel="teams", sus_width=1)), ("width 4", dict(sus_kernel="teams",
-                    sus_width=4)), ("levels", dict(sus_kernel="levels"))):
+    for name, v in (("one team", dict(layout="lanes", sus_width=1)), ("width 4", dict(layout="lanes",
+                    sus_width=4)), ("levels", dict(layout="thread"))):
         m = to_dev(msg0.astype(np.float32))
         o = gfbp.step(cd, to_dev(b.obs, torch.float32), m, channel=b.channel, schedule="sus", T=b.T, K=b.K,
                       prior_in=prior, frame_param=fp, **v)
@@ -113,6 +115,64 @@ def test_wave_lockstep_step_equals_single_team(torch_cuda, oracle):
         outs[name] = {k: x.cpu().numpy() for k, x in o.items() if x is not None}
     _same(outs["one team"], outs["width 4"], "step width 4")
     _same(outs["one team"], outs["levels"], "step levels")
+
+
+@pytest.mark.parametrize("name,N,frames,max_iter", [
+    ("gf4_n96_bsc005", None, 64, 60),
+    ("gf16_n1000_awgn", 400, 36, 60),
+    ("gf8_n2000_markov_bsc", 300, 18, 40),
+    ("gf8_n2000_markov_bec", 300, 18, 40),
+])
+def test_pus_thread_layout_equals_lanes(torch_cuda, name, N, frames, max_iter):
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch(name, frames=frames, N=N)
+    cd = gfbp.Code.from_coo(b.code)
+    kw = dict(T=b.T, K=b.K, post=True, trace=True)
+    ref = gpu_decode(cd, b.obs, b.channel, b.param, "pus", max_iter, layout="lanes", **kw)
+    out = gpu_decode(cd, b.obs, b.channel, b.param, "pus", max_iter, layout="thread", **kw)
+    _same(ref, out, "pus thread layout")
+
+
+def test_pus_thread_layout_irregular_and_syndrome(torch_cuda):
+    """Row degree 12, column degree 6 (the lane kernel's large-degree variant)
+    and a nonzero syndrome."""
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    code = W.regular_code(8, 120, dv=6, dc=12, cfg="levels_dv6", encodable=False)
+    rng = np.random.default_rng(5)
+    F = 12
+    x = rng.integers(0, 8, size=(F, code.N))
+    z = code.syndrome(x).astype(np.uint8)
+    obs = W.bsc(rng, x, code.p, 0.04)
+    cd = gfbp.Code.from_coo(code)
+    for sched in ("pus", "sus"):
+        ref = gpu_decode(cd, obs, "bsc", 0.04, sched, 30, syndrome=z, post=True, trace=True, layout="lanes")
+        out = gpu_decode(cd, obs, "bsc", 0.04, sched, 30, syndrome=z, post=True, trace=True, layout="thread")
+        if sched == "pus":
+            _same(ref, out, "pus thread layout")
+        else:
+            # column degree 6 is beyond the SUS team kernels: the lane layout
+            # ran the generic group kernel, whose sums run in another order
+            assert np.mean(ref["x_hat"] == out["x_hat"]) > 0.99
+
+
+def test_pus_lockstep_thread_equals_lanes(torch_cuda, oracle):
+    import torch
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch("gf8_n2000_markov_bsc", frames=8, N=300)
+    cd = gfbp.Code.from_coo(b.code)
+    F = b.obs.shape[0]
+    msg0 = oracle.initial_messages(b.code, b.obs, b.channel, b.param, T=b.T, K=b.K)
+    _, pi = oracle.markov(b.T, np.full((1, b.code.q), 1.0 / b.code.q))
+    prior = to_dev(np.broadcast_to(pi, (F, b.K, b.code.q)).astype(np.float32).copy())
+    fp = to_dev(np.asarray(b.param, np.float32))
+    outs = {}
+    for lay in ("lanes", "thread"):
+        m = to_dev(msg0.astype(np.float32))
+        o = gfbp.step(cd, to_dev(b.obs, torch.float32), m, channel=b.channel, schedule="pus", T=b.T, K=b.K,
+                      prior_in=prior, frame_param=fp, layout=lay)
+        torch.cuda.synchronize()
+        outs[lay] = {k: x.cpu().numpy() for k, x in o.items() if x is not None}
+    _same(outs["lanes"], outs["thread"], "pus step thread layout")
 
 
 def test_levels_column_degree_above_team_limit(torch_cuda, oracle):
@@ -131,7 +191,7 @@ def test_levels_column_degree_above_team_limit(torch_cuda, oracle):
     for it in range(3):
         ref = oracle.step(code, obs, "bsc", 0.03, msg, "sus")
         o = gfbp.step(cd, to_dev(obs, torch.float32), to_dev(msg.astype(np.float32)), channel="bsc",
-                      schedule="sus", frame_param=fp, sus_kernel="levels")
+                      schedule="sus", frame_param=fp, layout="thread")
         torch.cuda.synchronize()
         assert np.abs(o["post"].cpu().numpy() - ref["post"]).max() <= LOCKSTEP_ATOL
         assert np.abs(o["msg"].cpu().numpy() - ref["msg"]).max() <= LOCKSTEP_ATOL
@@ -147,4 +207,4 @@ def test_wave_width_is_validated(torch_cuda):
         gfbp.decode(cd, to_dev(b.obs, torch.float32), b.channel, float(b.param[0]), schedule="sus", sus_width=3)
     with pytest.raises(KeyError):
         gfbp.decode(cd, to_dev(b.obs, torch.float32), b.channel, float(b.param[0]), schedule="sus",
-                    sus_kernel="fastest")
+                    layout="fastest")
