@@ -136,6 +136,9 @@ typedef enum { GFBP_CHECK_AUTO = 0, GFBP_CHECK_TRANSFORM = 1, GFBP_CHECK_DIRECT 
  *           pairs run at once, a thread each.
  *   AUTO    THREAD for SUS, LANES for PUS (the faster of the two on the
  *           GF(16) N = 1000 benchmark batch).
+ * SUS with the TRANSFORM check node (any q) also runs by levels unless LANES
+ * is asked for: a lane group per (column, check) pair instead of per frame,
+ * the same bits as the lane kernel.
  */
 typedef enum { GFBP_LAYOUT_AUTO = 0, GFBP_LAYOUT_LANES = 1, GFBP_LAYOUT_THREAD = 2 } gfbp_layout;
 

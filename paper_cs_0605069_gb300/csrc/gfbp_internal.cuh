@@ -583,6 +583,7 @@ int sus_auto_width(const DecodeArgs& A, int num_sms);
 bool sus_level_eligible(const DecodeArgs& A);
 bool pus_regs_eligible(const DecodeArgs& A);
 cudaError_t launch_sus_level(const DecodeArgs& A, int num_sms, cudaStream_t s);
+cudaError_t launch_sus_level_tr(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s);

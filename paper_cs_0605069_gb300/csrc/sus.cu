@@ -57,7 +57,10 @@ cudaError_t launch_init_q(const DecodeArgs& A, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
-    if (A.layout != GFBP_LAYOUT_LANES && sus_level_eligible(A)) return launch_sus_level(A, num_sms, s);
+    if (A.layout != GFBP_LAYOUT_LANES) {
+        if (sus_level_eligible(A)) return launch_sus_level(A, num_sms, s);
+        if (A.method == kTransform) return launch_sus_level_tr(A, num_sms, s);
+    }
     if (sus_team_eligible(A)) {
         const int w = A.width ? A.width : sus_auto_width(A, num_sms);
         return w > 1 ? launch_sus_wave(A, w, num_sms, s) : launch_sus_team(A, num_sms, s);

@@ -208,3 +208,47 @@ def test_wave_width_is_validated(torch_cuda):
     with pytest.raises(KeyError):
         gfbp.decode(cd, to_dev(b.obs, torch.float32), b.channel, float(b.param[0]), schedule="sus",
                     layout="fastest")
+
+
+@pytest.mark.parametrize("q,N,db", [(32, 192, 2.0), (64, 128, 2.5), (256, 96, 3.0), (16, 240, 1.5)])
+def test_sus_levels_transform_route_equals_lanes(torch_cuda, q, N, db):
+    """The level schedule with the transform check node (one lane group per
+    (column, check) pair) against the lane kernel walking the columns."""
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    code = W.regular_code(q, N, cfg=f"levels_tr_{q}", encodable=False)
+    rng = np.random.default_rng(q)
+    F = 10
+    x = rng.integers(0, q, size=(F, code.N))
+    z = code.syndrome(x).astype(np.uint8)
+    sig = W.ebn0_to_sigma(db)
+    obs = W.biawgn(rng, x, code.p, sig)
+    cd = gfbp.Code.from_coo(code)
+    kw = dict(syndrome=z, post=True, trace=True, check_method="transform")
+    ref = gpu_decode(cd, obs, "awgn", sig, "sus", 25, layout="lanes", **kw)
+    out = gpu_decode(cd, obs, "awgn", sig, "sus", 25, layout="thread", **kw)
+    _same(ref, out, f"GF({q}) levels, transform route")
+
+
+def test_sus_levels_transform_route_markov_step(torch_cuda, oracle):
+    import torch
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch("gf8_n2000_markov_bsc", frames=6, N=300)
+    cd = gfbp.Code.from_coo(b.code)
+    F = b.obs.shape[0]
+    msg0 = oracle.initial_messages(b.code, b.obs, b.channel, b.param, T=b.T, K=b.K)
+    _, pi = oracle.markov(b.T, np.full((1, b.code.q), 1.0 / b.code.q))
+    prior = to_dev(np.broadcast_to(pi, (F, b.K, b.code.q)).astype(np.float32).copy())
+    fp = to_dev(np.asarray(b.param, np.float32))
+    outs = {}
+    for lay in ("lanes", "thread"):
+        m = to_dev(msg0.astype(np.float32))
+        o = gfbp.step(cd, to_dev(b.obs, torch.float32), m, channel=b.channel, schedule="sus", T=b.T, K=b.K,
+                      prior_in=prior, frame_param=fp, layout=lay, check_method="transform")
+        torch.cuda.synchronize()
+        outs[lay] = {k: x.cpu().numpy() for k, x in o.items() if x is not None}
+    _same(outs["lanes"], outs["thread"], "sus step, transform route, levels")
+    full = {}
+    for lay in ("lanes", "thread"):
+        full[lay] = gpu_decode(cd, b.obs, b.channel, b.param, "sus", 30, T=b.T, K=b.K, post=True,
+                               check_method="transform", layout=lay)
+    _same(full["lanes"], full["thread"], "sus decode, transform route, Markov, levels")
