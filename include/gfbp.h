@@ -122,8 +122,9 @@ typedef struct {
 typedef enum { GFBP_CHECK_AUTO = 0, GFBP_CHECK_TRANSFORM = 1, GFBP_CHECK_DIRECT = 2 } gfbp_check_method;
 
 /*
- * How the kernels for q = 4, 8, 16 with the DIRECT check node hold a
- * q-vector.  Both layouts give the same bits.
+ * How the kernels for q <= 16 with the DIRECT check node hold a q-vector.
+ * Both layouts give the same bits (for SUS with q >= 4; at q = 2 the lane
+ * layout runs the generic group kernel, whose sums run in another order).
  *   LANES   spread over a group of lanes.  PUS: a lane group per check and
  *           per column.  SUS: lane teams walk the columns in order; with
  *           sus_width > 1 teams per frame, a column starts once the last
@@ -263,17 +264,25 @@ gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n_items, gfb
 gfbp_status gfbp_batch_run(gfbp_batch* batch, void* stream);
 /* Kernel variant chosen for every item (host [n_items]; values as in gfbp_autotune). */
 gfbp_status gfbp_batch_variants(const gfbp_batch* batch, int32_t* variants);
+/* Pin the kernel variant of every item (host [n_items], values as in
+ * gfbp_autotune); each must be one that gfbp_autotune may choose for the
+ * item's q and the batch's schedule (GFBP_EINVAL otherwise, nothing changed).
+ * Synchronous; not during a run of the batch. */
+gfbp_status gfbp_batch_set_variants(gfbp_batch* batch, const int32_t* variants);
 void gfbp_batch_destroy(gfbp_batch* batch);
 
 /*
- * Autotuner: time every kernel variant that computes the same arithmetic for
- * this code and schedule (for SUS with q <= 16: one lane team per frame with a
- * slot per check, or one lane group per frame) on the caller's sample of
- * n_frames frames, and remember the fastest for codes of the same (q, N, M, E)
- * and schedule on this device; later gfbp_batch_create calls use it.
+ * Autotuner: time every kernel variant that computes the same check-node
+ * route for this code and schedule (SUS: the level schedule with a CTA per
+ * frame, the team kernel with a warp per frame (q = 4, 8, 16), the group
+ * kernel with a lane group per frame) on the caller's sample of n_frames
+ * frames, and remember the fastest for codes of the same (q, N, M, E) and
+ * schedule on this device; later gfbp_batch_create calls use it.
  * Synchronous; allocates its own scratch.  *chosen receives the variant:
  * 0-2 team q = 4/8/16, 3-6 group probability route q = 2/4/8/16,
- * 7-10 group transform route q = 32/64/128/256.
+ * 7-10 group transform route q = 32/64/128/256, 11-14 levels probability
+ * route q = 2/4/8/16, 15-18 levels transform route q = 32/64/128/256 (the
+ * default without tuning: 11-18).  PUS has one variant per q.
  */
 gfbp_status gfbp_autotune(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
                           gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter, void* stream,

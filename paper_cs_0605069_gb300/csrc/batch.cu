@@ -2,8 +2,13 @@
 // persistent launch (per schedule) over a device frame table, with no host
 // synchronisation or allocation after gfbp_batch_create, so that a run can be
 // captured in a CUDA graph and replayed.  Each item carries the kernel variant
-// that decodes its frames (team or group SUS, probability or transform check
-// node), chosen by the autotuner (gfbp_autotune) or by default rules.
+// that decodes its frames, chosen by the autotuner (gfbp_autotune) or by
+// default rules.  SUS variants come in two families: the level schedules (a
+// CTA per frame: a thread per (column, check) pair for the probability route,
+// a lane group per pair for the transform route) and the column walkers (a
+// warp per frame: team or group kernels); a run launches one persistent
+// kernel per family present, each over the frame table, skipping the other
+// family's frames.
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -14,6 +19,8 @@
 
 #include "pus_frame.cuh"
 #include "sus_group.cuh"
+#include "sus_level.cuh"
+#include "sus_level_tr.cuh"
 #include "sus_team.cuh"
 
 namespace gfbp {
@@ -37,8 +44,14 @@ enum Variant : int {
     kTeam4 = 0, kTeam8, kTeam16,                              // SUS team, probability route
     kGroup2D, kGroup4D, kGroup8D, kGroup16D,                  // SUS group, probability route
     kGroup32T, kGroup64T, kGroup128T, kGroup256T,             // SUS group, transform route
+    kLevel2D, kLevel4D, kLevel8D, kLevel16D,                  // SUS levels, probability route (CTA family)
+    kLevel32T, kLevel64T, kLevel128T, kLevel256T,             // SUS levels, transform route (CTA family)
     kNumVariants
 };
+
+__host__ __device__ constexpr bool cta_variant(int v) { return v >= kLevel2D; }
+
+constexpr int kMixedCtaThreads = 128;   // SUS CTA family: one frame per CTA
 
 // Shared scratch per warp (floats) for the SUS variants.
 constexpr int kWarpScratch = 3 * 256 + 4;  // the largest: group q=256 transform route, one group per warp
@@ -62,6 +75,33 @@ __device__ __noinline__ void pus_call(const DecodeArgs& A, int f, const uint8_t*
     pus_frame<Q, 6, 3, METHOD>(A, f, ex, lg, sc);
 }
 
+template <int Q>
+__device__ __noinline__ void sus_level_call(const DecodeArgs& A, int f, const uint8_t* mul, const uint8_t* div,
+                                            float* dyn) {
+    sus_level_frame<Q, 8, kMixedCtaThreads>(A, f, mul, div, dyn, dyn + kLevelPiece * (Q + 1));
+}
+
+template <int Q>
+__device__ __noinline__ void sus_level_tr_call(const DecodeArgs& A, int f, const uint8_t* ex, const uint8_t* lg,
+                                               float* dyn) {
+    constexpr int G = Lay<Q>::G;
+    float* sc = dyn + (size_t)level_tr_sub<Q>() * Q + (size_t)(threadIdx.x / G) * (Q + 4);
+    sus_level_tr_frame<Q, kMixedCtaThreads>(A, f, ex, lg, dyn, sc);
+}
+
+// Dynamic shared memory of the CTA family: the largest over its variants.
+template <int Q>
+constexpr size_t level_mixed_floats() {
+    return Q <= 16 ? (size_t)(kLevelPiece + kMixedCtaThreads) * (Q + 1)
+                   : (size_t)level_tr_sub<Q>() * Q + (size_t)(kMixedCtaThreads / Lay<Q>::G) * (Q + 4);
+}
+constexpr size_t max2(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kMixedCtaSmem =
+    sizeof(float) * max2(max2(max2(level_mixed_floats<2>(), level_mixed_floats<4>()),
+                              max2(level_mixed_floats<8>(), level_mixed_floats<16>())),
+                         max2(max2(level_mixed_floats<32>(), level_mixed_floats<64>()),
+                              max2(level_mixed_floats<128>(), level_mixed_floats<256>())));
+
 // Index of the item holding global frame g (prefix sums, binary search).
 __device__ __forceinline__ int find_item(const int* __restrict__ prefix, int n_items, int g) {
     int lo = 0, hi = n_items - 1;
@@ -78,8 +118,8 @@ __device__ __forceinline__ int find_item(const int* __restrict__ prefix, int n_i
 struct FieldTables {
     uint8_t ex[8][512];
     uint8_t lg[8][256];
-    uint8_t mul[3][256];
-    uint8_t div[3][256];
+    uint8_t mul[4][256];   // q = 2, 4, 8, 16
+    uint8_t div[4][256];
 };
 
 __device__ void load_fields(FieldTables& T, const DecodeArgs* items, const int* field_item, int tid, int nt) {
@@ -90,9 +130,10 @@ __device__ void load_fields(FieldTables& T, const DecodeArgs* items, const int* 
         for (int x = tid; x < 256; x += nt) T.lg[p][x] = items[i].c.glog[x];
     }
     __syncthreads();
-    if (field_item[1] >= 0) team_tables<4>(T.ex[1], T.lg[1], T.mul[0], T.div[0], tid, nt);
-    if (field_item[2] >= 0) team_tables<8>(T.ex[2], T.lg[2], T.mul[1], T.div[1], tid, nt);
-    if (field_item[3] >= 0) team_tables<16>(T.ex[3], T.lg[3], T.mul[2], T.div[2], tid, nt);
+    if (field_item[0] >= 0) team_tables<2>(T.ex[0], T.lg[0], T.mul[0], T.div[0], tid, nt);
+    if (field_item[1] >= 0) team_tables<4>(T.ex[1], T.lg[1], T.mul[1], T.div[1], tid, nt);
+    if (field_item[2] >= 0) team_tables<8>(T.ex[2], T.lg[2], T.mul[2], T.div[2], tid, nt);
+    if (field_item[3] >= 0) team_tables<16>(T.ex[3], T.lg[3], T.mul[3], T.div[3], tid, nt);
     __syncthreads();
 }
 
@@ -117,9 +158,11 @@ __global__ void __launch_bounds__(kMixedThreads) k_sus_mixed(const DecodeArgs* _
         const int pf = A.c.p - 1;
         const uint8_t* ex = T.ex[pf];
         const uint8_t* lg = T.lg[pf];
-        const uint8_t* s_mul_it = T.mul[pf >= 1 && pf <= 3 ? pf - 1 : 0];
-        const uint8_t* s_div_it = T.div[pf >= 1 && pf <= 3 ? pf - 1 : 0];
-        switch (__ldg(variant + it)) {
+        const uint8_t* s_mul_it = T.mul[pf <= 3 ? pf : 0];
+        const uint8_t* s_div_it = T.div[pf <= 3 ? pf : 0];
+        const int var = __ldg(variant + it);
+        if (cta_variant(var)) continue;   // decoded by the CTA-family kernel
+        switch (var) {
         case kTeam4:
             if (lane < TeamLay<4>::TEAM)
                 sus_team_call<4>(A, f, s_mul_it, s_div_it, wscr + (lane / TeamLay<4>::GS) * (2 * 4 + 4));
@@ -156,6 +199,45 @@ __global__ void __launch_bounds__(kMixedThreads) k_sus_mixed(const DecodeArgs* _
             break;
         }
         __syncwarp();
+    }
+}
+
+// SUS, CTA family: one frame per CTA (level schedules).
+__global__ void __launch_bounds__(kMixedCtaThreads) k_sus_mixed_cta(const DecodeArgs* __restrict__ items,
+                                                                    const int* __restrict__ prefix,
+                                                                    const int* __restrict__ variant, int n_items,
+                                                                    int total, int* counter, const int* field_item) {
+    __shared__ FieldTables T;
+    __shared__ int s_frame;
+    extern __shared__ __align__(16) float s_dyn[];
+    const int tid = threadIdx.x;
+    load_fields(T, items, field_item, tid, blockDim.x);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_frame = atomicAdd(counter, 1);
+        __syncthreads();
+        const int gidx = s_frame;
+        if (gidx >= total) break;
+        const int it = find_item(prefix, n_items, gidx);
+        const int var = __ldg(variant + it);
+        if (!cta_variant(var)) continue;   // decoded by the warp-family kernel
+        const int f = gidx - __ldg(prefix + it);
+        const DecodeArgs& A = items[it];
+        const int pf = A.c.p - 1;
+        const uint8_t* ex = T.ex[pf];
+        const uint8_t* lg = T.lg[pf];
+        const uint8_t* mul = T.mul[pf <= 3 ? pf : 0];
+        const uint8_t* div = T.div[pf <= 3 ? pf : 0];
+        switch (var) {
+        case kLevel2D: sus_level_call<2>(A, f, mul, div, s_dyn); break;
+        case kLevel4D: sus_level_call<4>(A, f, mul, div, s_dyn); break;
+        case kLevel8D: sus_level_call<8>(A, f, mul, div, s_dyn); break;
+        case kLevel16D: sus_level_call<16>(A, f, mul, div, s_dyn); break;
+        case kLevel32T: sus_level_tr_call<32>(A, f, ex, lg, s_dyn); break;
+        case kLevel64T: sus_level_tr_call<64>(A, f, ex, lg, s_dyn); break;
+        case kLevel128T: sus_level_tr_call<128>(A, f, ex, lg, s_dyn); break;
+        default: sus_level_tr_call<256>(A, f, ex, lg, s_dyn); break;
+        }
     }
 }
 
@@ -196,25 +278,30 @@ __global__ void __launch_bounds__(kPusThreads) k_pus_mixed(const DecodeArgs* __r
 
 int default_variant(int q) {
     switch (q) {
-    case 2: return kGroup2D;
-    case 4: return kTeam4;
-    case 8: return kTeam8;
-    case 16: return kTeam16;
-    case 32: return kGroup32T;
-    case 64: return kGroup64T;
-    case 128: return kGroup128T;
-    default: return kGroup256T;
+    case 2: return kLevel2D;
+    case 4: return kLevel4D;
+    case 8: return kLevel8D;
+    case 16: return kLevel16D;
+    case 32: return kLevel32T;
+    case 64: return kLevel64T;
+    case 128: return kLevel128T;
+    default: return kLevel256T;
     }
 }
 
-// SUS variants the autotuner may pick from (same arithmetic route, so the
-// same results up to the order of rounding).
+// SUS variants the autotuner may pick from (same check-node route, so the
+// same results up to the order of rounding; level and team kernels of one q
+// give the same bits).
 std::vector<int> sus_candidates(int q) {
     switch (q) {
-    case 4: return {kTeam4, kGroup4D};
-    case 8: return {kTeam8, kGroup8D};
-    case 16: return {kTeam16, kGroup16D};
-    default: return {default_variant(q)};
+    case 2: return {kLevel2D, kGroup2D};
+    case 4: return {kLevel4D, kTeam4, kGroup4D};
+    case 8: return {kLevel8D, kTeam8, kGroup8D};
+    case 16: return {kLevel16D, kTeam16, kGroup16D};
+    case 32: return {kLevel32T, kGroup32T};
+    case 64: return {kLevel64T, kGroup64T};
+    case 128: return {kLevel128T, kGroup128T};
+    default: return {kLevel256T, kGroup256T};
     }
 }
 
@@ -258,13 +345,24 @@ bool field_owners(const std::vector<const gfbp_code*>& codes, int* owner, std::s
     return true;
 }
 
-void mixed_shape(MixedLaunch& m) {
+void mixed_shape(MixedLaunch& m, const int* variants) {
     int occ = 1;
     if (m.schedule == GFBP_SUS) {
+        m.has_cta = m.has_warp = false;
+        for (int i = 0; i < m.n_items; i++) (cta_variant(variants[i]) ? m.has_cta : m.has_warp) = true;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_mixed, kMixedThreads, 0);
         const long long want = ((long long)m.total + 3) / 4;
         const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
         m.grid = (int)(want < cap ? want : cap);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_sus_mixed_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixedCtaSmem);
+            attr = true;
+        }
+        int occ2 = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_sus_mixed_cta, kMixedCtaThreads, kMixedCtaSmem);
+        const long long cap2 = (long long)num_sms() * (occ2 > 0 ? occ2 : 1);
+        m.grid_cta = (int)(m.total < cap2 ? m.total : cap2);
     } else {
         m.pus_smem = sizeof(float) * (size_t)kMixedPusScratch;
         cudaFuncSetAttribute(k_pus_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.pus_smem);
@@ -276,12 +374,16 @@ void mixed_shape(MixedLaunch& m) {
 
 cudaError_t mixed_launch(const MixedLaunch& m, cudaStream_t s) {
     if (m.total == 0 || m.grid == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(m.d_counter, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(m.d_counter, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    if (m.schedule == GFBP_SUS)
-        k_sus_mixed<<<m.grid, kMixedThreads, 0, s>>>(m.d_args, m.d_prefix, m.d_variant, m.n_items, m.total,
-                                                     m.d_counter, m.d_field);
-    else
+    if (m.schedule == GFBP_SUS) {
+        if (m.has_cta)
+            k_sus_mixed_cta<<<m.grid_cta, kMixedCtaThreads, kMixedCtaSmem, s>>>(
+                m.d_args, m.d_prefix, m.d_variant, m.n_items, m.total, m.d_counter + 1, m.d_field);
+        if (m.has_warp)
+            k_sus_mixed<<<m.grid, kMixedThreads, 0, s>>>(m.d_args, m.d_prefix, m.d_variant, m.n_items, m.total,
+                                                         m.d_counter, m.d_field);
+    } else
         k_pus_mixed<<<m.grid, kPusThreads, m.pus_smem, s>>>(m.d_args, m.d_prefix, m.n_items, m.total, m.d_counter,
                                                             m.d_field);
     return cudaGetLastError();
@@ -394,7 +496,7 @@ extern "C" gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n
         delete b;
         return GFBP_ECUDA;
     }
-    mixed_shape(m);
+    mixed_shape(m, b->variant.data());
     *out = b;
     return GFBP_OK;
 }
@@ -421,6 +523,32 @@ extern "C" gfbp_status gfbp_batch_run(gfbp_batch* b, void* stream_v) {
 extern "C" gfbp_status gfbp_batch_variants(const gfbp_batch* b, int32_t* variants) {
     if (!b || !variants) { set_error("gfbp_batch_variants: NULL argument"); return GFBP_EINVAL; }
     for (size_t i = 0; i < b->variant.size(); i++) variants[i] = b->variant[i];
+    return GFBP_OK;
+}
+
+extern "C" gfbp_status gfbp_batch_set_variants(gfbp_batch* b, const int32_t* variants) {
+    if (!b || !variants) { set_error("gfbp_batch_set_variants: NULL argument"); return GFBP_EINVAL; }
+    const int n = (int)b->variant.size();
+    std::vector<int> v(n);
+    for (int i = 0; i < n; i++) {
+        const int q = b->args[i].c.q;
+        const std::vector<int> ok = b->m.schedule == GFBP_SUS ? sus_candidates(q) : std::vector<int>{default_variant(q)};
+        bool found = false;
+        for (int c : ok) found |= (c == variants[i]);
+        if (!found) {
+            set_error("gfbp_batch_set_variants: variant " + std::to_string(variants[i]) + " cannot decode item " +
+                      std::to_string(i) + " (q = " + std::to_string(q) + ")");
+            return GFBP_EINVAL;
+        }
+        v[i] = variants[i];
+    }
+    cudaError_t e = cudaMemcpy(b->m.d_variant, v.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_error(std::string("gfbp_batch_set_variants: ") + cudaGetErrorString(e));
+        return GFBP_ECUDA;
+    }
+    b->variant = v;
+    mixed_shape(b->m, b->variant.data());
     return GFBP_OK;
 }
 
@@ -463,6 +591,7 @@ extern "C" gfbp_status gfbp_autotune(const gfbp_code* code, int32_t n_frames, co
         b->variant[0] = v;
         e = cudaMemcpy(b->m.d_variant, &v, sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) break;
+        mixed_shape(b->m, b->variant.data());
         float ms = 0.f;
         for (int rep = 0; rep < 3 && st == GFBP_OK; rep++) {   // first run warms up
             cudaEventRecord(e0, s);

@@ -603,9 +603,11 @@ struct MixedLaunch {
     int schedule = 0;
     int grid = 0;
     size_t pus_smem = 0;
+    int grid_cta = 0;        // SUS: CTA-family kernel (level schedules)
+    bool has_cta = false, has_warp = false;
 };
 
-void mixed_shape(MixedLaunch& m);
+void mixed_shape(MixedLaunch& m, const int* variants);
 cudaError_t mixed_launch(const MixedLaunch& m, cudaStream_t s);
 int tuned_variant(const gfbp_code* code, int schedule);
 cudaError_t launch_fill_prior(const DecodeArgs& A, cudaStream_t s);

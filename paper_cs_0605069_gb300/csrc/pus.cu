@@ -70,12 +70,13 @@ cudaError_t launch_regs_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
 }  // namespace
 
 bool pus_regs_eligible(const DecodeArgs& A) {
-    return A.method == kDirect && A.c.q >= 4 && A.c.q <= 16;
+    return A.method == kDirect && A.c.q <= 16;
 }
 
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     if (A.layout == GFBP_LAYOUT_THREAD && pus_regs_eligible(A)) {
         switch (A.c.q) {
+        case 2: return launch_regs_q<2>(A, num_sms, s);
         case 4: return launch_regs_q<4>(A, num_sms, s);
         case 8: return launch_regs_q<8>(A, num_sms, s);
         case 16: return launch_regs_q<16>(A, num_sms, s);

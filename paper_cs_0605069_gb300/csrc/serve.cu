@@ -223,7 +223,7 @@ cudaError_t launch_round(gfbp_server* S, int schedule, const std::vector<Req*>& 
     if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_variant, variant.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_field, owner, sizeof(owner), cudaMemcpyHostToDevice, S->stream);
     if (e != cudaSuccess) return e;
-    mixed_shape(m);
+    mixed_shape(m, variant.data());
     return mixed_launch(m, S->stream);
 }
 

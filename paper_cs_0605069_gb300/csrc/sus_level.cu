@@ -32,11 +32,12 @@ cudaError_t launch_level_t(const DecodeArgs& A, int num_sms, cudaStream_t s) {
 }  // namespace
 
 bool sus_level_eligible(const DecodeArgs& A) {
-    return A.method == kDirect && A.c.q >= 4 && A.c.q <= 16;
+    return A.method == kDirect && A.c.q <= 16;
 }
 
 cudaError_t launch_sus_level(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     switch (A.c.q) {
+    case 2: return launch_level_t<2>(A, num_sms, s);
     case 4: return launch_level_t<4>(A, num_sms, s);
     case 8: return launch_level_t<8>(A, num_sms, s);
     case 16: return launch_level_t<16>(A, num_sms, s);

@@ -33,19 +33,29 @@ namespace {
 
 template <int Q>
 __device__ __forceinline__ void ldq(float (&x)[Q], const float* p) {
+    if constexpr (Q == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(p);
+        x[0] = a.x; x[1] = a.y;
+    } else {
 #pragma unroll
-    for (int i = 0; i < Q; i += 4) {
-        const float4 a = *reinterpret_cast<const float4*>(p + i);
-        x[i] = a.x; x[i + 1] = a.y; x[i + 2] = a.z; x[i + 3] = a.w;
+        for (int i = 0; i < Q; i += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(p + i);
+            x[i] = a.x; x[i + 1] = a.y; x[i + 2] = a.z; x[i + 3] = a.w;
+        }
     }
 }
 
 template <int Q>
 __device__ __forceinline__ void ldgq(float (&x)[Q], const float* p) {
+    if constexpr (Q == 2) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+        x[0] = a.x; x[1] = a.y;
+    } else {
 #pragma unroll
-    for (int i = 0; i < Q; i += 4) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(p + i));
-        x[i] = a.x; x[i + 1] = a.y; x[i + 2] = a.z; x[i + 3] = a.w;
+        for (int i = 0; i < Q; i += 4) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(p + i));
+            x[i] = a.x; x[i + 1] = a.y; x[i + 2] = a.z; x[i + 3] = a.w;
+        }
     }
 }
 
@@ -58,15 +68,20 @@ __device__ __forceinline__ void prefetch_l1(const void* p, int bytes) {
 
 template <int Q>
 __device__ __forceinline__ void stq(float* p, const float (&x)[Q]) {
+    if constexpr (Q == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+    } else {
 #pragma unroll
-    for (int i = 0; i < Q; i += 4) *reinterpret_cast<float4*>(p + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+        for (int i = 0; i < Q; i += 4)
+            *reinterpret_cast<float4*>(p + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+    }
 }
 
 // U <- U (*) Y, (U (*) Y)[y] = sum_x U[x] Y[x XOR y]: partial p over x = 4p..4p+3
 // in increasing x (one FMA chain), partials added in increasing p.
 template <int Q>
 __device__ __forceinline__ void xconv_regs(float (&U)[Q], const float (&Y)[Q]) {
-    constexpr int NP = Q / 4;
+    constexpr int NP = Q >= 4 ? Q / 4 : 1, XL = Q >= 4 ? 4 : Q;
     float o[Q];
 #pragma unroll
     for (int p = 0; p < NP; p++) {
@@ -74,7 +89,7 @@ __device__ __forceinline__ void xconv_regs(float (&U)[Q], const float (&Y)[Q]) {
 #pragma unroll
         for (int y = 0; y < Q; y++) t[y] = fmaf(U[4 * p], Y[(4 * p) ^ y], 0.f);
 #pragma unroll
-        for (int xl = 1; xl < 4; xl++) {
+        for (int xl = 1; xl < XL; xl++) {
             const int x = 4 * p + xl;
 #pragma unroll
             for (int y = 0; y < Q; y++) t[y] = fmaf(U[x], Y[x ^ y], t[y]);

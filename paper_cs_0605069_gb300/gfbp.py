@@ -27,7 +27,8 @@ LAYOUT = {"auto": 0, "lanes": 1, "thread": 2}
 # Functions declared in include/gfbp.h (the CPU test checks that every one is exported).
 EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info",
            "gfbp_workspace_size", "gfbp_decode", "gfbp_step", "gfbp_decode_noalloc",
-           "gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_batch_destroy", "gfbp_autotune",
+           "gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_batch_set_variants",
+           "gfbp_batch_destroy", "gfbp_autotune",
            "gfbp_server_create", "gfbp_server_submit", "gfbp_server_wait", "gfbp_server_stats",
            "gfbp_server_drain", "gfbp_server_destroy")
 
@@ -264,10 +265,12 @@ def _batch_lib():
                                         C.POINTER(C.c_void_p)]
         L.gfbp_batch_run.argtypes = [P, P]
         L.gfbp_batch_variants.argtypes = [P, C.POINTER(i32)]
+        L.gfbp_batch_set_variants.argtypes = [P, C.POINTER(i32)]
         L.gfbp_batch_destroy.argtypes = [P]
         L.gfbp_batch_destroy.restype = None
         L.gfbp_autotune.argtypes = [P, i32, P, gfbp_channel, i32, C.POINTER(gfbp_prior), i32, P, C.POINTER(i32)]
-        for fn in ("gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_autotune"):
+        for fn in ("gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_batch_set_variants",
+                   "gfbp_autotune"):
             getattr(L, fn).restype = C.c_int
         L._batch_typed = True
     return L
@@ -313,6 +316,11 @@ class Batch:
         v = (C.c_int32 * self.n)()
         _ok(_batch_lib().gfbp_batch_variants(self.handle, v), "gfbp_batch_variants")
         return list(v)
+
+    def set_variants(self, variants):
+        """Pin every item's kernel variant (numbering of gfbp_autotune)."""
+        v = (C.c_int32 * self.n)(*[int(x) for x in variants])
+        _ok(_batch_lib().gfbp_batch_set_variants(self.handle, v), "gfbp_batch_set_variants")
 
     def close(self):
         if getattr(self, "handle", None):

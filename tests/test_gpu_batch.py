@@ -83,7 +83,7 @@ def test_autotune_picks_a_valid_variant_and_batches_use_it(env):
     obs = torch.from_numpy(b0.obs).cuda()
     fp = torch.from_numpy(b0.param.astype(np.float32)).cuda()
     v = gfbp.autotune(code, obs, "awgn", 0.0, schedule="sus", max_iter=10, frame_param=fp)
-    assert v in (2, 6)                      # team or group, both probability route for q = 16
+    assert v in (14, 2, 6)                  # levels, team or group: the probability route for q = 16
     b = gfbp.Batch([dict(code=code, obs=obs, channel="awgn", frame_param=fp)], schedule="sus", max_iter=30)
     assert b.variants() == [v]
     outs = b.run()
@@ -102,3 +102,43 @@ def test_batch_rejects_bad_items(env):
     with pytest.raises(gfbp.GfbpError) as e:
         gfbp.Batch([dict(code=cd, obs=torch.zeros((2, 8, 2), device="cuda"), channel="bsc", param=0.1)])
     assert e.value.status == gfbp.GFBP_EUNSUPPORTED
+
+
+# variant numbers of gfbp_autotune
+TEAM = {4: 0, 8: 1, 16: 2}
+GROUP_D = {2: 3, 4: 4, 8: 5, 16: 6}
+GROUP_T = {32: 7, 64: 8, 128: 9, 256: 10}
+LEVEL = {2: 11, 4: 12, 8: 13, 16: 14, 32: 15, 64: 16, 128: 17, 256: 18}
+
+
+def test_batch_default_variants_are_level_schedules(env):
+    torch, gfbp, W = env
+    items = _mixed_items(torch, gfbp, W, frames=4)
+    b = gfbp.Batch(items, schedule="sus", max_iter=5)
+    assert b.variants() == [LEVEL[it["code"].q] for it in items]
+    b.close()
+
+
+def test_batch_with_both_kernel_families_equals_each_code_alone(env):
+    """Items pinned to warp-per-frame variants (team q=4, group transform
+    q=64) beside items on the level schedules (q=16, q=256, q=2): the two
+    persistent kernels of one run split the frame table between them, and
+    every item still equals gfbp_decode of its code alone (level, team and
+    group transform kernels give the same bits)."""
+    torch, gfbp, W = env
+    items = _mixed_items(torch, gfbp, W)
+    qs = [it["code"].q for it in items]
+    pin = {4: TEAM[4], 16: LEVEL[16], 64: GROUP_T[64], 256: LEVEL[256], 2: LEVEL[2]}
+    b = gfbp.Batch(items, schedule="sus", max_iter=40)
+    b.set_variants([pin[q] for q in qs])
+    assert b.variants() == [pin[q] for q in qs]
+    outs = b.run()
+    torch.cuda.synchronize()
+    for it, o in zip(items, outs):
+        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule="sus", max_iter=40)
+        torch.cuda.synchronize()
+        for k in ("x_hat", "iters", "converged"):
+            assert torch.equal(ref[k], o[k]), (it["code"].q, k)
+    with pytest.raises(gfbp.GfbpError):
+        b.set_variants([TEAM[16] for _ in qs])   # a q=16 variant for every item
+    b.close()
