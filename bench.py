@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sus-width", type=int, default=0, help="SUS lane teams per frame (0 = automatic)")
     ap.add_argument("--layout", default="auto", choices=["auto", "lanes", "thread"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve", "wht"],
                     help="batch: the GF(16) N=1000 benchmark (default); mixed: frames of 12 (q, N) classes in one "
                          "persistent launch; serve: Poisson arrivals to the continuous-batching server")
     ap.add_argument("--duration", type=float, default=6.0, help="serve: seconds per offered load")
@@ -60,6 +60,12 @@ def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def measured_peaks():
+    """The measured HBM copy bandwidth and bf16 GEMM rates, or None."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else None
 
 
 class ClockSampler:
@@ -203,6 +209,10 @@ def main():
     if args.workload == "serve":
         from bench_modes import run_serve
         run_serve(args)
+        return
+    if args.workload == "wht":
+        from bench_modes import run_wht
+        run_wht(args)
         return
     import torch
     torch.cuda.set_device(local)

@@ -1,5 +1,5 @@
-"""Measurements of the batched and served forms (python bench.py --workload
-mixed | serve); one JSON line each.  Inputs are synthetic: noisy all-zero
+"""Measurements of the batched and served forms and of the transform kernels
+(python bench.py --workload mixed | serve | wht); one JSON line each.  Inputs are synthetic: noisy all-zero
 codewords over symmetric channels (a linear code's BP trajectory does not
 depend on the codeword), regular (3,6) codes from the seeded generator."""
 from __future__ import annotations
@@ -174,3 +174,55 @@ def run_serve(args):
                        "budget_bytes": budget, "round_iters": 4, "duration_s": args.duration},
             "saturation_frames_per_s": sat, "sweep": sweep, "server": st, "clocks": clocks}
     print(json.dumps(line), flush=True)
+
+
+def run_wht(args):
+    """gfbp_wht on 2 GB of q-vectors per q in {64, 128, 256}: FP32 butterflies
+    on the CUDA cores against the FP16 hi/lo contraction on the tensor cores
+    (bytes moved: the vectors read once and written once; tensor flops: 2 q^2
+    per vector per FP16 part)."""
+    import torch
+    from bench import ClockSampler, measured_peaks
+    from paper_cs_0605069_gb300 import gfbp
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    res = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for q in (64, 128, 256):
+        n = (2 << 30) // (4 * q)
+        g = torch.Generator(device="cuda").manual_seed(q)
+        x = torch.rand((n, q), device="cuda", generator=g)
+        x /= x.sum(1, keepdim=True)
+        y = torch.empty_like(x)
+        row = {}
+        for m in ("simt", "tensor"):
+            for _ in range(max(args.warmup, 3)):
+                gfbp.wht(x, m, out=y)
+            ts = []
+            for _ in range(args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                gfbp.wht(x, m, out=y)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = float(np.median(ts))
+            gbs = 2 * x.numel() * 4 / (ms / 1e3) / 1e9
+            row[m] = {"ms": ms, "vectors_per_s": n / (ms / 1e3), "GB_s": gbs,
+                      "frac_hbm": gbs / peaks["hbm_gbs"] if peaks else None}
+            if m == "tensor":
+                tf = 2 * 2 * n * q * q / (ms / 1e3) / 1e12
+                row[m]["tensor_TFLOP_s"] = tf
+        ys = gfbp.wht(x[:4096], "simt")
+        yt = gfbp.wht(x[:4096], "tensor")
+        row["max_abs_diff_tensor_vs_simt"] = float((ys - yt).abs().max().item())
+        res[f"q{q}"] = row
+        del x, y
+    cl = clocks.stop()
+    line = {"metric": "Walsh-Hadamard transforms/s, FP32 CUDA-core butterflies vs FP16 hi/lo tensor cores",
+            "workload": "wht", "unit": "vectors/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "value": res["q256"]["tensor"]["vectors_per_s"], "higher_is_better": True, "dtype": "f32 (tensor: f16x2 in, f32 acc)",
+            "data": "synthetic probability vectors, 2 GB per q (above L2)", "config": {"bytes_per_q": 2 << 30},
+            "per_q": res, "clocks": cl}
+    print(json.dumps(line))

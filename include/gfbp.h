@@ -231,6 +231,24 @@ gfbp_status gfbp_step(const gfbp_code* code, int32_t n_frames, const float* obs,
                       float* prior_out, float* post, uint8_t* x_hat, uint8_t* sat,
                       const gfbp_options* options, void* stream);
 
+/* ------------------------------------------------ Walsh-Hadamard transform */
+/*
+ * y[v] = WHT(x[v]) for n q-vectors: y[b] = sum_a (-1)^popcount(a AND b) x[a],
+ * the transform behind the convolution theorem of Eq. 3 (unnormalised; apply
+ * it twice and divide by q for the identity).  x, y: device [n][q] float32,
+ * 16-byte aligned; y may equal x.
+ *   GFBP_WHT_SIMT    FP32 butterflies on the CUDA cores (any q).
+ *   GFBP_WHT_TENSOR  dense +-1 contraction on the tensor cores: each x split
+ *                    into FP16 high and low parts (|x| < 65504), FP32
+ *                    accumulation; q in {16, ..., 256}.  Each vector is
+ *                    scaled by a power of two to a largest |x| in [1, 2)
+ *                    first (undone exactly).  Error per output below
+ *                    2^-19 sum_a |x[a]| + q 2^-24 max_a |x[a]| (tested).
+ * Enqueued on `stream`.
+ */
+typedef enum { GFBP_WHT_SIMT = 0, GFBP_WHT_TENSOR = 1 } gfbp_wht_method;
+gfbp_status gfbp_wht(const float* x, float* y, int64_t n, int32_t q, int32_t method, void* stream);
+
 /* --------------------------------------------------------------- batching */
 /*
  * Frames of several codes — uneven q and N — decoded by one persistent launch

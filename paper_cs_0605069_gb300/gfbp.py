@@ -28,7 +28,7 @@ LAYOUT = {"auto": 0, "lanes": 1, "thread": 2}
 EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info",
            "gfbp_workspace_size", "gfbp_decode", "gfbp_step", "gfbp_decode_noalloc",
            "gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_batch_set_variants",
-           "gfbp_batch_destroy", "gfbp_autotune",
+           "gfbp_batch_destroy", "gfbp_autotune", "gfbp_wht",
            "gfbp_server_create", "gfbp_server_submit", "gfbp_server_wait", "gfbp_server_stats",
            "gfbp_server_drain", "gfbp_server_destroy")
 
@@ -75,8 +75,9 @@ def lib() -> C.CDLL:
             L.gfbp_step.argtypes = [P, i32, P, gfbp_channel, i32, C.POINTER(gfbp_prior), P, P, P, P, P, P,
                                     C.POINTER(gfbp_options), P]
             L.gfbp_decode_noalloc.argtypes = L.gfbp_decode.argtypes
+            L.gfbp_wht.argtypes = [P, P, i64, i32, i32, P]
             for fn in ("gfbp_code_create", "gfbp_code_info", "gfbp_workspace_size", "gfbp_decode", "gfbp_step",
-                       "gfbp_decode_noalloc"):
+                       "gfbp_decode_noalloc", "gfbp_wht"):
                 getattr(L, fn).restype = C.c_int
             _lib = L
     return _lib
@@ -222,6 +223,21 @@ def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedul
                         _ptr(prior_out), _ptr(post), _ptr(x_hat), _ptr(sat), C.byref(opt), _stream(stream)),
         "gfbp_step")
     return dict(msg=msg, post=post, x_hat=x_hat, sat=sat, prior_out=prior_out)
+
+
+WHT_METHOD = {"simt": 0, "tensor": 1}
+
+
+def wht(x, method: str = "simt", out=None, stream=None):
+    """gfbp_wht on a CUDA float32 tensor [n, q] (unnormalised Walsh-Hadamard
+    transform of every row); method "simt" (FP32 butterflies) or "tensor"
+    (FP16 hi/lo split on the tensor cores, FP32 accumulation)."""
+    import torch
+    x = x.contiguous()
+    n, q = int(x.shape[0]), int(x.shape[1])
+    y = torch.empty_like(x) if out is None else out
+    _ok(lib().gfbp_wht(_ptr(x), _ptr(y), n, q, WHT_METHOD[method], _stream(stream)), "gfbp_wht")
+    return y
 
 
 def decode_noalloc(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: str = "pus",
