@@ -117,9 +117,20 @@ typedef struct {
  *   DIRECT     the configuration sum by successive XOR-convolutions of the
  *              relabelled messages, non-negative arithmetic only, every entry
  *              to relative precision (q <= 16).
+ *   TENSOR     the convolution theorem with plain transforms stored (F =
+ *              WHT of the relabelled q), the transforms inside the sweep taken
+ *              as dense +-1 Hadamard contractions on the tensor cores (FP16
+ *              hi/lo split of power-of-two-scaled vectors, FP32 accumulation;
+ *              gfbp_wht).  SUS only, q >= 16; posteriors within 1e-4 of the
+ *              FP64 oracle per iteration (tested).
  *   AUTO       DIRECT for q <= 16, TRANSFORM above.
  */
-typedef enum { GFBP_CHECK_AUTO = 0, GFBP_CHECK_TRANSFORM = 1, GFBP_CHECK_DIRECT = 2 } gfbp_check_method;
+typedef enum {
+    GFBP_CHECK_AUTO = 0,
+    GFBP_CHECK_TRANSFORM = 1,
+    GFBP_CHECK_DIRECT = 2,
+    GFBP_CHECK_TENSOR = 3
+} gfbp_check_method;
 
 /*
  * How the kernels for q <= 16 with the DIRECT check node hold a q-vector.

@@ -298,11 +298,16 @@ gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const flo
         set_error("check_method DIRECT needs q <= 16");
         return GFBP_EUNSUPPORTED;
     }
-    if (m < GFBP_CHECK_AUTO || m > GFBP_CHECK_DIRECT) {
+    if (m < GFBP_CHECK_AUTO || m > GFBP_CHECK_TENSOR) {
         set_error("unknown check_method");
         return GFBP_EINVAL;
     }
-    A.method = (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > 16)) ? kTransform : kDirect;
+    if (m == GFBP_CHECK_TENSOR && c.q < 16) {
+        set_error("check_method TENSOR needs q >= 16");
+        return GFBP_EUNSUPPORTED;
+    }
+    A.method = m == GFBP_CHECK_TENSOR ? kTensor
+             : (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > 16)) ? kTransform : kDirect;
     A.width = opt ? opt->sus_width : 0;
     A.layout = opt ? opt->layout : GFBP_LAYOUT_AUTO;
     if (A.layout < GFBP_LAYOUT_AUTO || A.layout > GFBP_LAYOUT_THREAD) {
@@ -354,6 +359,10 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
     DecodeArgs A;
     gfbp_status st = fill_args(A, code, F, obs, ch, C, max_iter, step, x_hat, iters, conv, msg_io, prior_out, opt);
     if (st != GFBP_OK) return st;
+    if (A.method == kTensor && schedule != GFBP_SUS) {
+        set_error("check_method TENSOR is implemented for SUS only");
+        return GFBP_EUNSUPPORTED;
+    }
 
     void* ws = opt ? opt->workspace : nullptr;
     bool own = false;

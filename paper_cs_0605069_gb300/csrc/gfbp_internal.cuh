@@ -573,7 +573,7 @@ __device__ __forceinline__ void markov_prior(const DecodeArgs& A, int f, int i, 
 // Launchers (one instantiation set per schedule, see pus.cu / sus.cu).
 // Check-node arithmetic: probability-domain convolution (q <= 16) or the
 // deviation transform (any q).
-enum Method { kDirect = 0, kTransform = 1 };
+enum Method { kDirect = 0, kTransform = 1, kTensor = 2 };
 
 cudaError_t launch_channel(const DecodeArgs& A, cudaStream_t s);
 bool sus_team_eligible(const DecodeArgs& A);
@@ -584,6 +584,7 @@ bool sus_level_eligible(const DecodeArgs& A);
 bool pus_regs_eligible(const DecodeArgs& A);
 cudaError_t launch_sus_level(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus_level_tr(const DecodeArgs& A, int num_sms, cudaStream_t s);
+cudaError_t launch_sus_level_tc(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_init_dev(const DecodeArgs& A, cudaStream_t s);
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s);

@@ -50,6 +50,12 @@ cudaError_t launch_init_q(const DecodeArgs& A, cudaStream_t s) {
             return cudaGetLastError();
         }
     }
+    if constexpr (Q >= 16) {
+        if (A.method == kTensor) {
+            k_init_dev<Q, kTensor><<<(unsigned)blocks, 256, 0, s>>>(A);
+            return cudaGetLastError();
+        }
+    }
     k_init_dev<Q, kTransform><<<(unsigned)blocks, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
@@ -57,6 +63,7 @@ cudaError_t launch_init_q(const DecodeArgs& A, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    if (A.method == kTensor) return launch_sus_level_tc(A, num_sms, s);
     if (A.layout != GFBP_LAYOUT_LANES) {
         if (sus_level_eligible(A)) return launch_sus_level(A, num_sms, s);
         if (A.method == kTransform) return launch_sus_level_tr(A, num_sms, s);

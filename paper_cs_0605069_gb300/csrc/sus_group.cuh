@@ -360,8 +360,15 @@ __global__ void __launch_bounds__(256) k_init_dev(const DecodeArgs A) {
         float x[V];
         if (A.step) ldv<V>(x, A.msg_io + (size_t)it * Q + g * V);
         else prior_vec<Q>(A, f, A.c.ecol[e], x, mask, g);
-        if constexpr (METHOD == kDirect) to_relabelled<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
-        else to_deviation<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+        if constexpr (METHOD == kDirect) {
+            to_relabelled<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+        } else if constexpr (METHOD == kTensor) {
+            // the plain transform of the relabelled q (FP32 butterflies)
+            to_relabelled<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+            wht<Q>(x, mask, g);
+        } else {
+            to_deviation<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
+        }
         stv<V>(A.msg + (size_t)it * Q + g * V, x);
     }
 }

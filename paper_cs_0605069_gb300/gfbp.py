@@ -21,7 +21,7 @@ _lock = threading.Lock()
 GFBP_OK, GFBP_EINVAL, GFBP_ENOMEM, GFBP_ECUDA, GFBP_ETIMEOUT, GFBP_EBUSY, GFBP_EUNSUPPORTED = range(7)
 CHANNEL = {"bsc": 0, "bec": 1, "awgn": 2, "biawgn": 2, "loglik": 3}
 SCHEDULE = {"pus": 0, "sus": 1}
-CHECK_METHOD = {"auto": 0, "transform": 1, "direct": 2}
+CHECK_METHOD = {"auto": 0, "transform": 1, "direct": 2, "tensor": 3}
 LAYOUT = {"auto": 0, "lanes": 1, "thread": 2}
 
 # Functions declared in include/gfbp.h (the CPU test checks that every one is exported).

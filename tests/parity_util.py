@@ -90,3 +90,12 @@ def classify_frames(gpu, ora, gap_thr=TIE_GAP, horizon=None):
         else:
             kinds.append("fail")
     return np.array(kinds)
+
+
+class Batchlike:
+    """The fields of a workload batch that the free-running parity check reads,
+    for inputs built in a test (i.i.d. source)."""
+
+    def __init__(self, code, obs, param, max_iter):
+        self.code, self.obs, self.param, self.max_iter = code, obs, param, max_iter
+        self.T, self.K = None, 0

@@ -254,3 +254,51 @@ def test_single_frame_and_large_batch_agree(torch_cuda, schedule):
         assert one["iters"][0] == full["iters"][f]
         np.testing.assert_array_equal(one["x_hat"][0], full["x_hat"][f])
         np.testing.assert_array_equal(one["post"][0], full["post"][f])
+
+
+# The TENSOR check method (SUS, q >= 16): transforms on the tensor cores with an
+# FP16 hi/lo split and FP32 accumulation; the stated bound is 1e-4 posterior
+# max-abs per iteration against the FP64 oracle.
+TENSOR_ATOL = 1e-4
+
+
+@pytest.mark.parametrize("q,N,db", [(64, 128, 2.0), (256, 48, 2.5), (16, 240, 1.5)])
+def test_lockstep_tensor_route(torch_cuda, oracle, q, N, db):
+    from paper_cs_0605069_gb300 import workload as W
+    code = W.regular_code(q, N, cfg=f"tensor_route_{q}", encodable=False)
+    rng = np.random.default_rng(q + 7)
+    F = 8
+    x = rng.integers(0, q, size=(F, code.N))
+    sig = W.ebn0_to_sigma(db)
+    obs = W.biawgn(rng, x, code.p, sig)
+    worst = _lockstep(torch_cuda, oracle, code, obs, "awgn", np.full(F, sig), "sus", iters=6,
+                      method="tensor", atol=TENSOR_ATOL)
+    print(f"GF({q}) tensor route lock-step worst {worst:.2e}")
+
+
+def test_lockstep_tensor_route_markov(torch_cuda, oracle):
+    from paper_cs_0605069_gb300 import workload as W
+    b = W.make_batch("gf8_n2000_markov_bsc", frames=4, N=300)
+    # GF(8) is below the tensor route's q >= 16: the route is refused there
+    from paper_cs_0605069_gb300 import gfbp
+    import torch
+    cd = gfbp.Code.from_coo(b.code)
+    with pytest.raises(gfbp.GfbpError):
+        gfbp.decode(cd, to_dev(b.obs, torch.float32), "bsc", 0.08, schedule="sus", check_method="tensor")
+    with pytest.raises(gfbp.GfbpError):
+        code64 = W.regular_code(64, 64, cfg="tensor_pus", encodable=False)
+        c64 = gfbp.Code.from_coo(code64)
+        obs = torch.zeros((2, 64, 6), device="cuda")
+        gfbp.decode(c64, obs, "awgn", 0.8, schedule="pus", check_method="tensor")
+
+
+def test_free_running_tensor_route_gf64(torch_cuda, oracle):
+    from paper_cs_0605069_gb300 import workload as W
+    from tests.parity_util import Batchlike
+    code = W.regular_code(64, 256, cfg="tensor_free_64", encodable=False)
+    rng = np.random.default_rng(64)
+    F = 48
+    x = np.zeros((F, code.N), np.int64)
+    sig = np.array([W.ebn0_to_sigma(db) for db in (1.5, 2.0, 2.5)])[np.arange(F) % 3]
+    obs = W.biawgn(rng, x, code.p, sig)
+    _free_running(oracle, Batchlike(code, obs, sig, 40), "awgn", "sus", method="tensor")
