@@ -24,7 +24,9 @@ def run_mixed(args):
     """12 classes (q in {4,16,64,256} x N in {256,1000,4000}), frames
     round-robin over the classes, BI-AWGN 1.5 dB, SUS, max 200 iterations:
     one persistent launch captured in a CUDA graph (kernel variants from the
-    autotuner) against one gfbp_decode launch per class."""
+    autotuner) against one gfbp_decode launch per class, and the same graph
+    with the q >= 64 classes on the tensor-core transforms (FP16 hi/lo split,
+    FP32 accumulation) instead of the FP32 CUDA-core transforms."""
     import torch
     from paper_cs_0605069_gb300 import gfbp, workload as W
     total = args.frames if args.frames != 4096 else 8192
@@ -81,6 +83,39 @@ def run_mixed(args):
     torch.cuda.synchronize()
     plain_ms = a.elapsed_time(z)
     frames = per * len(classes)
+
+    # the q >= 64 classes on the tensor-core route (variant numbers of gfbp_autotune)
+    tensor_variant = {64: 21, 128: 22, 256: 23}
+    bt = gfbp.Batch(items, schedule="sus", max_iter=max_iter)
+    bt.set_variants([tensor_variant.get(it["code"].q, v) for it, v in zip(items, b.variants())])
+    with torch.cuda.stream(s):
+        bt.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    gt = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gt):
+        bt.run(stream=torch.cuda.current_stream())
+    for _ in range(args.warmup):
+        gt.replay()
+    evt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, z in evt:
+        a.record()
+        gt.replay()
+        z.record()
+    torch.cuda.synchronize()
+    ms_t = float(np.mean([a.elapsed_time(z) for a, z in evt]))
+    agree = {}
+    for (q, N), o, ot in zip(classes, b.outputs, bt.outputs):
+        if q in tensor_variant:
+            same = (o["x_hat"] == ot["x_hat"]).all(1) & (o["iters"] == ot["iters"])
+            agree[f"q{q}_N{N}"] = {"same_decisions_and_iters": float(same.float().mean().item()),
+                                   "converged_fp32": float(o["converged"].float().mean().item()),
+                                   "converged_tensor": float(ot["converged"].float().mean().item())}
+    tensor = {"ms_per_step": ms_t, "value": frames / (ms_t / 1e3), "variants": dict(zip([f"q{q}_N{N}" for q, N in classes],
+                                                                                    bt.variants())),
+              "vs_fp32_transforms": agree,
+              "posterior_accuracy": "both routes within 1e-4 posterior max-abs of the FP64 oracle per iteration "
+                                    "(tests/test_gpu_parity.py lock-step)"}
     line = {"metric": "decoded frames/s, mixed (q, N) batch in one persistent graph-captured launch", "workload": "mixed",
             "value": frames / (ms / 1e3), "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
@@ -89,7 +124,7 @@ def run_mixed(args):
                        "channel": "BI-AWGN Eb/N0 1.5 dB", "max_iter": max_iter, "graph": True},
             "sym_iter_per_s": symit / (ms / 1e3), "variants": dict(zip([f"q{q}_N{N}" for q, N in classes],
                                                                        b.variants())),
-            "autotuned": tuned, "plain_per_class_ms": plain_ms,
+            "autotuned": tuned, "plain_per_class_ms": plain_ms, "tensor_core_transforms": tensor,
             "mean_iters": {f"q{q}_N{N}": float(o["iters"].float().mean().item())
                            for (q, N), o in zip(classes, b.outputs)},
             "clocks": clocks}

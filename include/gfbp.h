@@ -311,7 +311,9 @@ void gfbp_batch_destroy(gfbp_batch* batch);
  * 0-2 team q = 4/8/16, 3-6 group probability route q = 2/4/8/16,
  * 7-10 group transform route q = 32/64/128/256, 11-14 levels probability
  * route q = 2/4/8/16, 15-18 levels transform route q = 32/64/128/256 (the
- * default without tuning: 11-18).  PUS has one variant per q.
+ * default without tuning: 11-18).  PUS has one variant per q.  Variants 19-23
+ * (levels, TENSOR check method, q = 16/32/64/128/256) are never chosen here;
+ * gfbp_batch_set_variants takes them.
  */
 gfbp_status gfbp_autotune(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
                           gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter, void* stream,

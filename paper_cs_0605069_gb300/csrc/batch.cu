@@ -9,6 +9,7 @@
 // warp per frame: team or group kernels); a run launches one persistent
 // kernel per family present, each over the frame table, skipping the other
 // family's frames.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -20,6 +21,7 @@
 #include "pus_frame.cuh"
 #include "sus_group.cuh"
 #include "sus_level.cuh"
+#include "sus_level_tc.cuh"
 #include "sus_level_tr.cuh"
 #include "sus_team.cuh"
 
@@ -46,12 +48,32 @@ enum Variant : int {
     kGroup32T, kGroup64T, kGroup128T, kGroup256T,             // SUS group, transform route
     kLevel2D, kLevel4D, kLevel8D, kLevel16D,                  // SUS levels, probability route (CTA family)
     kLevel32T, kLevel64T, kLevel128T, kLevel256T,             // SUS levels, transform route (CTA family)
+    kLevel16X, kLevel32X, kLevel64X, kLevel128X, kLevel256X,  // SUS levels, tensor-core route (CTA family)
     kNumVariants
 };
 
+// Check-node route a variant computes (the item's DecodeArgs::method).
+int variant_method(int v) {
+    if (v >= kLevel16X) return kTensor;
+    if ((v >= kGroup32T && v <= kGroup256T) || (v >= kLevel32T && v <= kLevel256T)) return kTransform;
+    return kDirect;
+}
+
+int tensor_variant(int q) {
+    switch (q) {
+    case 16: return kLevel16X;
+    case 32: return kLevel32X;
+    case 64: return kLevel64X;
+    case 128: return kLevel128X;
+    case 256: return kLevel256X;
+    }
+    return -1;
+}
+
 __host__ __device__ constexpr bool cta_variant(int v) { return v >= kLevel2D; }
 
-constexpr int kMixedCtaThreads = 128;   // SUS CTA family: one frame per CTA
+// SUS CTA family: one frame per CTA, 256 threads when a transform-route item
+// (a lane group per pair) is in the launch, else 128 (a thread per pair).
 
 // Shared scratch per warp (floats) for the SUS variants.
 constexpr int kWarpScratch = 3 * 256 + 4;  // the largest: group q=256 transform route, one group per warp
@@ -75,32 +97,60 @@ __device__ __noinline__ void pus_call(const DecodeArgs& A, int f, const uint8_t*
     pus_frame<Q, 6, 3, METHOD>(A, f, ex, lg, sc);
 }
 
-template <int Q>
+template <int Q, int T>
 __device__ __noinline__ void sus_level_call(const DecodeArgs& A, int f, const uint8_t* mul, const uint8_t* div,
                                             float* dyn) {
-    sus_level_frame<Q, 8, kMixedCtaThreads>(A, f, mul, div, dyn, dyn + kLevelPiece * (Q + 1));
+    sus_level_frame<Q, 8, T>(A, f, mul, div, dyn, dyn + kLevelPiece * (Q + 1));
 }
 
-template <int Q>
+template <int Q, int T>
 __device__ __noinline__ void sus_level_tr_call(const DecodeArgs& A, int f, const uint8_t* ex, const uint8_t* lg,
                                                float* dyn) {
     constexpr int G = Lay<Q>::G;
     float* sc = dyn + (size_t)level_tr_sub<Q>() * Q + (size_t)(threadIdx.x / G) * (Q + 4);
-    sus_level_tr_frame<Q, kMixedCtaThreads>(A, f, ex, lg, dyn, sc);
+    sus_level_tr_frame<Q, T>(A, f, ex, lg, dyn, sc);
 }
 
-// Dynamic shared memory of the CTA family: the largest over its variants.
-template <int Q>
-constexpr size_t level_mixed_floats() {
-    return Q <= 16 ? (size_t)(kLevelPiece + kMixedCtaThreads) * (Q + 1)
-                   : (size_t)level_tr_sub<Q>() * Q + (size_t)(kMixedCtaThreads / Lay<Q>::G) * (Q + 4);
+template <int Q, int T>
+__device__ __noinline__ void sus_level_tc_call(const DecodeArgs& A, int f, const uint8_t* ex, const uint8_t* lg,
+                                               float* dyn) {
+    sus_level_tc_frame<Q, T>(A, f, ex, lg, reinterpret_cast<uint8_t*>(dyn));
+}
+
+// Dynamic shared memory of a CTA-family variant with T threads.
+template <int Q, int T>
+constexpr size_t level_mixed_bytes() {
+    return sizeof(float) * (Q <= 16 ? (size_t)(kLevelPiece + T) * (Q + 1)
+                                    : (size_t)level_tr_sub<Q>() * Q + (size_t)(T / Lay<Q>::G) * (Q + 4));
 }
 constexpr size_t max2(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kMixedCtaSmem =
-    sizeof(float) * max2(max2(max2(level_mixed_floats<2>(), level_mixed_floats<4>()),
-                              max2(level_mixed_floats<8>(), level_mixed_floats<16>())),
-                         max2(max2(level_mixed_floats<32>(), level_mixed_floats<64>()),
-                              max2(level_mixed_floats<128>(), level_mixed_floats<256>())));
+
+template <int T>
+size_t cta_variant_smem(int v) {
+    switch (v) {
+    case kLevel2D: return level_mixed_bytes<2, T>();
+    case kLevel4D: return level_mixed_bytes<4, T>();
+    case kLevel8D: return level_mixed_bytes<8, T>();
+    case kLevel16D: return level_mixed_bytes<16, T>();
+    case kLevel32T: return level_mixed_bytes<32, T>();
+    case kLevel64T: return level_mixed_bytes<64, T>();
+    case kLevel128T: return level_mixed_bytes<128, T>();
+    case kLevel256T: return level_mixed_bytes<256, T>();
+    case kLevel16X: return TcLay<16, T>::total;
+    case kLevel32X: return TcLay<32, T>::total;
+    case kLevel64X: return TcLay<64, T>::total;
+    case kLevel128X: return TcLay<128, T>::total;
+    case kLevel256X: return TcLay<256, T>::total;
+    }
+    return 0;
+}
+
+template <int T>
+constexpr size_t cta_smem_max() {
+    return max2(max2(max2(TcLay<64, T>::total, TcLay<256, T>::total), max2(TcLay<128, T>::total, TcLay<32, T>::total)),
+                max2(max2(level_mixed_bytes<256, T>(), level_mixed_bytes<64, T>()),
+                     max2(level_mixed_bytes<16, T>(), TcLay<16, T>::total)));
+}
 
 // Index of the item holding global frame g (prefix sums, binary search).
 __device__ __forceinline__ int find_item(const int* __restrict__ prefix, int n_items, int g) {
@@ -203,7 +253,8 @@ __global__ void __launch_bounds__(kMixedThreads) k_sus_mixed(const DecodeArgs* _
 }
 
 // SUS, CTA family: one frame per CTA (level schedules).
-__global__ void __launch_bounds__(kMixedCtaThreads) k_sus_mixed_cta(const DecodeArgs* __restrict__ items,
+template <int NTH>
+__global__ void __launch_bounds__(NTH, 512 / NTH) k_sus_mixed_cta(const DecodeArgs* __restrict__ items,
                                                                     const int* __restrict__ prefix,
                                                                     const int* __restrict__ variant, int n_items,
                                                                     int total, int* counter, const int* field_item) {
@@ -229,14 +280,19 @@ __global__ void __launch_bounds__(kMixedCtaThreads) k_sus_mixed_cta(const Decode
         const uint8_t* mul = T.mul[pf <= 3 ? pf : 0];
         const uint8_t* div = T.div[pf <= 3 ? pf : 0];
         switch (var) {
-        case kLevel2D: sus_level_call<2>(A, f, mul, div, s_dyn); break;
-        case kLevel4D: sus_level_call<4>(A, f, mul, div, s_dyn); break;
-        case kLevel8D: sus_level_call<8>(A, f, mul, div, s_dyn); break;
-        case kLevel16D: sus_level_call<16>(A, f, mul, div, s_dyn); break;
-        case kLevel32T: sus_level_tr_call<32>(A, f, ex, lg, s_dyn); break;
-        case kLevel64T: sus_level_tr_call<64>(A, f, ex, lg, s_dyn); break;
-        case kLevel128T: sus_level_tr_call<128>(A, f, ex, lg, s_dyn); break;
-        default: sus_level_tr_call<256>(A, f, ex, lg, s_dyn); break;
+        case kLevel2D: sus_level_call<2, NTH>(A, f, mul, div, s_dyn); break;
+        case kLevel4D: sus_level_call<4, NTH>(A, f, mul, div, s_dyn); break;
+        case kLevel8D: sus_level_call<8, NTH>(A, f, mul, div, s_dyn); break;
+        case kLevel16D: sus_level_call<16, NTH>(A, f, mul, div, s_dyn); break;
+        case kLevel32T: sus_level_tr_call<32, NTH>(A, f, ex, lg, s_dyn); break;
+        case kLevel64T: sus_level_tr_call<64, NTH>(A, f, ex, lg, s_dyn); break;
+        case kLevel128T: sus_level_tr_call<128, NTH>(A, f, ex, lg, s_dyn); break;
+        case kLevel256T: sus_level_tr_call<256, NTH>(A, f, ex, lg, s_dyn); break;
+        case kLevel16X: sus_level_tc_call<16, NTH>(A, f, ex, lg, s_dyn); break;
+        case kLevel32X: sus_level_tc_call<32, NTH>(A, f, ex, lg, s_dyn); break;
+        case kLevel64X: sus_level_tc_call<64, NTH>(A, f, ex, lg, s_dyn); break;
+        case kLevel128X: sus_level_tc_call<128, NTH>(A, f, ex, lg, s_dyn); break;
+        default: sus_level_tc_call<256, NTH>(A, f, ex, lg, s_dyn); break;
         }
     }
 }
@@ -345,22 +401,49 @@ bool field_owners(const std::vector<const gfbp_code*>& codes, int* owner, std::s
     return true;
 }
 
+// Order of a launch's frame table: items with the costliest frames first (the
+// frames are handed out in table order, so the longest decodes start first
+// instead of setting the tail).  Cost of a frame ~ N q (work per sweep up to a
+// log factor); ties keep the given order.
+std::vector<int> heavy_first(const std::vector<const CodeDev*>& codes) {
+    std::vector<int> order(codes.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)codes[a]->N * codes[a]->q > (long long)codes[b]->N * codes[b]->q;
+    });
+    return order;
+}
+
 void mixed_shape(MixedLaunch& m, const int* variants) {
     int occ = 1;
     if (m.schedule == GFBP_SUS) {
         m.has_cta = m.has_warp = false;
-        for (int i = 0; i < m.n_items; i++) (cta_variant(variants[i]) ? m.has_cta : m.has_warp) = true;
+        m.cta_threads = 128;
+        for (int i = 0; i < m.n_items; i++) {
+            (cta_variant(variants[i]) ? m.has_cta : m.has_warp) = true;
+            if (cta_variant(variants[i]) && variant_method(variants[i]) != kDirect) m.cta_threads = 256;
+        }
+        m.cta_smem = 0;
+        for (int i = 0; i < m.n_items; i++)
+            m.cta_smem = max2(m.cta_smem, m.cta_threads == 256 ? cta_variant_smem<256>(variants[i])
+                                                               : cta_variant_smem<128>(variants[i]));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_mixed, kMixedThreads, 0);
         const long long want = ((long long)m.total + 3) / 4;
         const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
         m.grid = (int)(want < cap ? want : cap);
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_sus_mixed_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixedCtaSmem);
+            cudaFuncSetAttribute(k_sus_mixed_cta<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cta_smem_max<128>());
+            cudaFuncSetAttribute(k_sus_mixed_cta<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cta_smem_max<256>());
             attr = true;
         }
         int occ2 = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_sus_mixed_cta, kMixedCtaThreads, kMixedCtaSmem);
+        if (m.cta_threads == 256)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_sus_mixed_cta<256>, 256, m.cta_smem);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_sus_mixed_cta<128>, 128, m.cta_smem);
         const long long cap2 = (long long)num_sms() * (occ2 > 0 ? occ2 : 1);
         m.grid_cta = (int)(m.total < cap2 ? m.total : cap2);
     } else {
@@ -378,8 +461,14 @@ cudaError_t mixed_launch(const MixedLaunch& m, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (m.schedule == GFBP_SUS) {
         if (m.has_cta)
-            k_sus_mixed_cta<<<m.grid_cta, kMixedCtaThreads, kMixedCtaSmem, s>>>(
-                m.d_args, m.d_prefix, m.d_variant, m.n_items, m.total, m.d_counter + 1, m.d_field);
+        {
+            if (m.cta_threads == 256)
+                k_sus_mixed_cta<256><<<m.grid_cta, 256, m.cta_smem, s>>>(m.d_args, m.d_prefix, m.d_variant, m.n_items,
+                                                                        m.total, m.d_counter + 1, m.d_field);
+            else
+                k_sus_mixed_cta<128><<<m.grid_cta, 128, m.cta_smem, s>>>(m.d_args, m.d_prefix, m.d_variant, m.n_items,
+                                                                        m.total, m.d_counter + 1, m.d_field);
+        }
         if (m.has_warp)
             k_sus_mixed<<<m.grid, kMixedThreads, 0, s>>>(m.d_args, m.d_prefix, m.d_variant, m.n_items, m.total,
                                                          m.d_counter, m.d_field);
@@ -402,13 +491,40 @@ int tuned_variant(const gfbp_code* code, int schedule) {
 }  // namespace gfbp
 
 struct gfbp_batch {
-    std::vector<gfbp::DecodeArgs> args;
-    std::vector<int> variant;
+    std::vector<gfbp::DecodeArgs> args;   // caller's item order
+    std::vector<int> variant;             // caller's item order
+    std::vector<int> order;               // frame-table position -> caller's item
     void* dmem = nullptr;  // items | prefix | variants | counter | field owners | per-item workspaces
     gfbp::MixedLaunch m;
 };
 
 using namespace gfbp;
+
+namespace {
+
+// The device frame table in b->order: items, frame prefix, variants, field
+// owners (synchronous).
+cudaError_t upload_tables(gfbp_batch* b) {
+    const int n = (int)b->args.size();
+    std::vector<DecodeArgs> a(n);
+    std::vector<int> prefix(n + 1, 0), v(n);
+    int owner[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    for (int k = 0; k < n; k++) {
+        const int i = b->order[k];
+        a[k] = b->args[i];
+        v[k] = b->variant[i];
+        prefix[k + 1] = prefix[k] + a[k].F;
+        const int pf = a[k].c.p - 1;
+        if (owner[pf] < 0) owner[pf] = k;
+    }
+    cudaError_t e = cudaMemcpy(b->m.d_args, a.data(), sizeof(DecodeArgs) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->m.d_prefix, prefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->m.d_variant, v.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->m.d_field, owner, sizeof(owner), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
 
 extern "C" gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n_items, gfbp_schedule schedule,
                                          int32_t max_iter, const gfbp_options* options, gfbp_batch** out) {
@@ -486,10 +602,12 @@ extern "C" gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n
         }
         b->variant[i] = tuned_variant(it.code, schedule);
     }
-    e = cudaMemcpy(m.d_args, b->args.data(), sizeof(DecodeArgs) * n_items, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m.d_prefix, prefix.data(), sizeof(int) * (n_items + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m.d_variant, b->variant.data(), sizeof(int) * n_items, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m.d_field, owner, sizeof(owner), cudaMemcpyHostToDevice);
+    {
+        std::vector<const CodeDev*> cd(n_items);
+        for (int i = 0; i < n_items; i++) cd[i] = &items[i].code->dev;
+        b->order = heavy_first(cd);
+    }
+    e = upload_tables(b);
     if (e != cudaSuccess) {
         set_error(std::string("gfbp_batch_create: ") + cudaGetErrorString(e));
         cudaFree(b->dmem);
@@ -532,7 +650,8 @@ extern "C" gfbp_status gfbp_batch_set_variants(gfbp_batch* b, const int32_t* var
     std::vector<int> v(n);
     for (int i = 0; i < n; i++) {
         const int q = b->args[i].c.q;
-        const std::vector<int> ok = b->m.schedule == GFBP_SUS ? sus_candidates(q) : std::vector<int>{default_variant(q)};
+        std::vector<int> ok = b->m.schedule == GFBP_SUS ? sus_candidates(q) : std::vector<int>{default_variant(q)};
+        if (b->m.schedule == GFBP_SUS && tensor_variant(q) >= 0) ok.push_back(tensor_variant(q));
         bool found = false;
         for (int c : ok) found |= (c == variants[i]);
         if (!found) {
@@ -542,12 +661,15 @@ extern "C" gfbp_status gfbp_batch_set_variants(gfbp_batch* b, const int32_t* var
         }
         v[i] = variants[i];
     }
-    cudaError_t e = cudaMemcpy(b->m.d_variant, v.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+    // a variant of another check-node route changes the stored message form
+    // (and the initialisation kernel of gfbp_batch_run)
+    for (int i = 0; i < n; i++) b->args[i].method = variant_method(v[i]);
+    b->variant = v;
+    cudaError_t e = upload_tables(b);
     if (e != cudaSuccess) {
         set_error(std::string("gfbp_batch_set_variants: ") + cudaGetErrorString(e));
         return GFBP_ECUDA;
     }
-    b->variant = v;
     mixed_shape(b->m, b->variant.data());
     return GFBP_OK;
 }

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/gfbp.h"
 
 namespace gfbp {
@@ -605,10 +607,13 @@ struct MixedLaunch {
     int grid = 0;
     size_t pus_smem = 0;
     int grid_cta = 0;        // SUS: CTA-family kernel (level schedules)
+    size_t cta_smem = 0;     // its dynamic shared memory (largest over the items' variants)
+    int cta_threads = 128;   // its threads per CTA
     bool has_cta = false, has_warp = false;
 };
 
 void mixed_shape(MixedLaunch& m, const int* variants);
+std::vector<int> heavy_first(const std::vector<const CodeDev*>& codes);
 cudaError_t mixed_launch(const MixedLaunch& m, cudaStream_t s);
 int tuned_variant(const gfbp_code* code, int schedule);
 cudaError_t launch_fill_prior(const DecodeArgs& A, cudaStream_t s);

@@ -186,8 +186,15 @@ cudaError_t launch_round(gfbp_server* S, int schedule, const std::vector<Req*>& 
     std::vector<DecodeArgs> items;
     std::vector<int> prefix(1, 0), variant;
     int owner[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    std::vector<Req*> sel;
+    std::vector<const CodeDev*> cd;
     for (Req* r : rs) {
         if (r->schedule != schedule) continue;
+        sel.push_back(r);
+        cd.push_back(&r->code->dev);
+    }
+    for (int i : heavy_first(cd)) {
+        Req* r = sel[i];
         const int pf = r->code->dev.p - 1;
         if (owner[pf] < 0) owner[pf] = (int)items.size();
         items.push_back(r->A);

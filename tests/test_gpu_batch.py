@@ -142,3 +142,24 @@ def test_batch_with_both_kernel_families_equals_each_code_alone(env):
     with pytest.raises(gfbp.GfbpError):
         b.set_variants([TEAM[16] for _ in qs])   # a q=16 variant for every item
     b.close()
+
+
+def test_batch_tensor_route_variants_equal_decode(env):
+    """Items pinned to the tensor-core route (variants 21, 23) decode as
+    gfbp_decode with check_method TENSOR does, bit for bit; the other items keep
+    the FP32 routes in the same run."""
+    torch, gfbp, W = env
+    items = _mixed_items(torch, gfbp, W, frames=12)
+    qs = [it["code"].q for it in items]
+    b = gfbp.Batch(items, schedule="sus", max_iter=30)
+    b.set_variants([{64: 21, 256: 23}.get(q, LEVEL[q]) for q in qs])
+    outs = b.run()
+    torch.cuda.synchronize()
+    for it, o in zip(items, outs):
+        q = it["code"].q
+        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule="sus", max_iter=30,
+                          check_method="tensor" if q in (64, 256) else "auto")
+        torch.cuda.synchronize()
+        for k in ("x_hat", "iters", "converged"):
+            assert torch.equal(ref[k], o[k]), (q, k)
+    b.close()
