@@ -32,6 +32,17 @@ WORKLOAD = "gf16_n1000_awgn"
 # writes every edge message twice per iteration plus the prior (52 q bytes); SUS
 # reads and writes the single stored slab once per sweep plus the prior (28 q).
 ALG_BYTES_PER_SYMITER = {"pus": 52, "sus": 28}
+# Algorithmic FP32 FMAs per symbol-iteration of the probability-domain check
+# node (q <= 16; d_v = 3, d_c = 6, M/N = 1/2): SUS folds the d_c - 1 other
+# edges of each of a column's 3 checks (4 convolutions of q^2 FMAs each):
+# 12 q^2; PUS runs 3 (d_c - 2) = 12 convolutions per check, M/N checks per
+# symbol: 6 q^2.
+ALG_FMA_PER_SYMITER_Q2 = {"pus": 6, "sus": 12}
+# FP32 FMA rate: 152 SMs x 4 schedulers x 32 lanes, one FMA (2 flop) per lane
+# per clock, at the sampled SM clock (2070 MHz maximum).
+FP32_LANES = 152 * 4 * 32
+# The kernel of each schedule on the benchmark path (layout AUTO).
+BENCH_KERNEL = {"pus": "k_pus<16,6,3,0>", "sus": "k_sus_level<16,8,128>"}
 
 
 def parse():
@@ -132,16 +143,23 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def files_hash(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel: str, symiters: float):
     """DRAM bytes of the kernel for this launch, scaled from the committed ncu
-    summary when it was taken on the current kernel source; else None."""
+    summary when it was taken on the kernel's current source files; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         t = json.load(open(path))
-    except (OSError, ValueError):
-        return None
-    ent = t.get(kernel)
-    if not ent or ent.get("source_hash") != source_hash():
+        ent = t.get(kernel)
+        if not ent or ent.get("source_hash") != files_hash(ent["files"]):
+            return None
+    except (OSError, ValueError, KeyError):
         return None
     return ent["dram_bytes_per_symiter"] * symiters
 
@@ -328,20 +346,29 @@ def main():
                   "iters_by_ebn0_db": {str(db): float(it[:, k::3].mean()) for k, db in enumerate((1.0, 1.5, 2.0))},
                   "converged": float(outs[s]["converged"].float().mean().item())}
         per[s]["mean_iters_converged"] = None
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: the FP32 FMA pipe (the probability-domain
+    # check node's q^2 convolutions) and the HBM model of the paper's passes;
+    # "bound" is the nearer of the two ceilings
     dom = max(scheds, key=lambda s: per[s]["kernel_ms"])
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     symit_launch = float(np.stack(iters[dom]).sum()) * N / args.steps
-    q_alg = ALG_BYTES_PER_SYMITER[dom]
-    alg_bytes = ALG_BYTES_PER_SYMITER[dom] * q * symit_launch
-    achieved = alg_bytes / (per[dom]["kernel_ms"] / 1e3) / 1e9
-    traffic = profiled_traffic("k_" + dom, symit_launch)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": f"k_{dom}<16,6,3>",
-            "peak_source": "measured" if peaks else "fallback",
-            "algorithmic_bytes_per_symiter": ALG_BYTES_PER_SYMITER[dom] * q}
+    secs = per[dom]["kernel_ms"] / 1e3
+    hbm_gbs = ALG_BYTES_PER_SYMITER[dom] * q * symit_launch / secs / 1e9
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    alu_peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    alu_tf = 2 * ALG_FMA_PER_SYMITER_Q2[dom] * q * q * symit_launch / secs / 1e12
+    kernel = BENCH_KERNEL[dom] if args.layout == "auto" and args.method == "auto" else None
+    traffic = profiled_traffic(kernel, symit_launch) if kernel else None
+    hbm = {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+           "peak_source": "measured" if peaks else "fallback",
+           "algorithmic_bytes_per_symiter": ALG_BYTES_PER_SYMITER[dom] * q}
+    alu = {"achieved": alu_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_tf / alu_peak,
+           "peak_source": f"derived: {FP32_LANES} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sampled SM clock)",
+           "algorithmic_flops_per_symiter": 2 * ALG_FMA_PER_SYMITER_Q2[dom] * q * q}
+    main, other, bound = (alu, hbm, "alu") if alu["frac"] >= hbm["frac"] else (hbm, alu, "hbm")
+    roof = {"bound": bound, **main, "traffic": traffic, "kernel": kernel or f"{dom} ({args.layout}/{args.method})",
+            ("hbm_model" if bound == "alu" else "alu_model"): other}
     gpu_launches = args.steps * sum(2 if s == "pus" else 3 for s in scheds)  # channel (+ SUS init) + decode
 
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
