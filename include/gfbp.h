@@ -196,7 +196,10 @@ gfbp_status gfbp_workspace_size(const gfbp_code* code, int32_t n_frames, gfbp_sc
  *   obs       device, see gfbp_channel_kind.
  *   max_iter  >= 1.
  *   x_hat     device [F][N]: decided symbols of the last iteration.
- *   iters     device [F]: iterations run (1..max_iter).
+ *   iters     device [F]: iterations run (1..max_iter); -1 marks a frame whose
+ *             decode gave up on an internal bounded wait (SUS with sus_width
+ *             > 1 only; no such wait is expected to run out), its x_hat and
+ *             converged flag are then not valid.
  *   converged device [F]: 1 when H x_hat = z.
  */
 gfbp_status gfbp_decode(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
