@@ -394,6 +394,22 @@ def markov_source(u: np.ndarray, T: np.ndarray, start: np.ndarray | None = None)
     return s
 
 
+def bit_chain_symbols(Tb: np.ndarray, p: int) -> np.ndarray:
+    """The first-order chain over p-bit symbols induced by a two-state bit
+    chain Tb run through bits 0..p-1 of every symbol in turn: Pr(next = b |
+    current = a) = Tb[a_{p-1}, b_0] Tb[b_0, b_1] ... Tb[b_{p-2}, b_{p-1}]."""
+    q = 1 << p
+    T = np.ones((q, q))
+    for a in range(q):
+        for b in range(q):
+            prev = (a >> (p - 1)) & 1
+            for k in range(p):
+                bit = (b >> k) & 1
+                T[a, b] *= Tb[prev, bit]
+                prev = bit
+    return T
+
+
 def self_transition_chain(q: int, stay: float) -> np.ndarray:
     """q-state chain that stays with probability `stay`, else moves uniformly."""
     T = np.full((q, q), (1.0 - stay) / (q - 1))
