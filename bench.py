@@ -67,6 +67,27 @@ def parse():
     return ap.parse_args()
 
 
+def shard_first_frame(rank: int, frames_per_rank: int) -> int:
+    """Weak scaling: rank r decodes frames r*F .. r*F + F - 1 of the workload."""
+    return rank * frames_per_rank
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's value (an all-reduce MAX; the only collective, outside
+    the timed region)."""
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_frames_per_s(frames_per_rank_step: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank's frames over the slowest rank's time."""
+    return frames_per_rank_step * world / (ms_per_step / 1e3)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -245,7 +266,7 @@ def main():
     from paper_cs_0605069_gb300 import gfbp, workload as W
 
     F = args.frames
-    b = W.make_batch(WORKLOAD, frames=F, first_frame=rank * F)
+    b = W.make_batch(WORKLOAD, frames=F, first_frame=shard_first_frame(rank, F))
     code = gfbp.Code.from_coo(b.code)
     N, q = b.code.N, b.code.q
     dev = torch.device("cuda", local)
@@ -291,15 +312,12 @@ def main():
             iters[s].append(outs[s]["iters"].cpu().numpy().copy())
     torch.cuda.synchronize()
     clocks = clk.stop()
-    total_ms = float(np.sum(step_ms))
+    total_ms = max_over_ranks(float(np.sum(step_ms)), world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
     frames_per_step = len(scheds) * F * world
-    value = frames_per_step / (ms_per_step / 1e3)
+    value = job_frames_per_s(len(scheds) * F, world, ms_per_step)
 
     # end to end through the public API: pinned host obs in, results out, every step
     e2e = None
@@ -333,12 +351,8 @@ def main():
             z.record(stream)
             torch.cuda.synchronize()
             e_ms.append(a.elapsed_time(z))
-        em = float(np.mean(e_ms))
-        if world > 1:
-            t = torch.tensor([em], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            em = float(t.item())
-        e2e = {"value": frames_per_step / (em / 1e3), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
+        em = max_over_ranks(float(np.mean(e_ms)), world, dev)
+        e2e = {"value": job_frames_per_s(len(scheds) * F, world, em), "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     per = {}
