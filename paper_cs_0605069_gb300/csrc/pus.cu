@@ -5,24 +5,36 @@ namespace gfbp {
 
 namespace {
 
-template <int Q, int DC, int DV, int METHOD>
-cudaError_t launch_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+template <int Q, int DC, int DV, int METHOD, bool BULK>
+cudaError_t launch_qb(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr int G = Lay<Q>::G;
-    constexpr size_t smem = sizeof(float) * (size_t)(kPusThreads / G) * pus_group_scratch<Q, DC, METHOD>();
+    constexpr size_t smem = sizeof(float) * (size_t)(kPusThreads / G) * pus_group_scratch<Q, DC, METHOD, BULK>();
     static int occ = -1;
     if (occ < 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_pus<Q, DC, DV, METHOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_pus<Q, DC, DV, METHOD, BULK>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus<Q, DC, DV, METHOD>, kPusThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus<Q, DC, DV, METHOD, BULK>, kPusThreads, smem);
         if (e != cudaSuccess) return e;
         if (occ < 1) occ = 1;
     }
     long long grid = (long long)num_sms * occ;
     if (grid > A.F) grid = A.F;
     if (grid < 1) return cudaSuccess;
-    k_pus<Q, DC, DV, METHOD><<<(int)grid, kPusThreads, smem, s>>>(A);
+    k_pus<Q, DC, DV, METHOD, BULK><<<(int)grid, kPusThreads, smem, s>>>(A);
     return cudaGetLastError();
+}
+
+// The bulk-staged kernel hides the latency of a check's loads behind the
+// previous check (GF(16) N = 1000, 1024 frames: 36.7 ms against 40.0 ms) but
+// its second buffer costs a CTA per SM, which loses once the frames fill the
+// GPU (4096 frames: 132 ms against 122 ms): it runs for at most 8 frames per SM.
+template <int Q, int DC, int DV, int METHOD>
+cudaError_t launch_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    if constexpr (pus_bulk_ok<Q, METHOD>()) {
+        if ((long long)A.F <= 8LL * num_sms) return launch_qb<Q, DC, DV, METHOD, true>(A, num_sms, s);
+    }
+    return launch_qb<Q, DC, DV, METHOD, false>(A, num_sms, s);
 }
 
 template <int Q, int METHOD>

@@ -12,6 +12,7 @@
 // one column).
 #pragma once
 
+#include "bulk.cuh"
 #include "gfbp_internal.cuh"
 
 namespace gfbp {
@@ -74,24 +75,30 @@ __device__ __forceinline__ void pus_check(const DecodeArgs& A, float* slab, int 
 // convolutions S_k = qt_{k+1} * ... * qt_{d-1}, a running prefix P, and
 // r_k from P * S_k (3(d-2) convolutions for d edges).  The group's scratch
 // holds the d stored vectors and two operand slots.
-template <int Q, int DC>
+// STAGED: the d stored vectors are already in `sc` (a bulk copy) and the
+// operand slots are at `ops`; otherwise they are copied in here and the slots
+// follow them.
+template <int Q, int DC, bool STAGED = false>
 __device__ __forceinline__ void pus_check_direct(const DecodeArgs& A, float* slab, int f, int i, float* sc,
-                                                 unsigned mask, int g, const uint8_t* ex, const uint8_t* lg) {
+                                                 unsigned mask, int g, const uint8_t* ex, const uint8_t* lg,
+                                                 float* ops = nullptr) {
     constexpr int V = Lay<Q>::V;
     const int e0 = A.c.rowptr[i];
     const int d = A.c.rowptr[i + 1] - e0;
     const int z = A.syn ? (A.syn[(size_t)f * A.c.M + i] & (Q - 1)) : 0;
-    float* T0 = sc + DC * Q;
+    float* T0 = STAGED ? ops : sc + DC * Q;
     float* T1 = T0 + Q;
+    if constexpr (!STAGED) {
 #pragma unroll
-    for (int k = 0; k < DC; k++) {
-        if (k < d) {
-            float x[V];
-            ldv<V>(x, slab + (size_t)(e0 + k) * Q + g * V);
-            stv<V>(sc + k * Q + g * V, x);
+        for (int k = 0; k < DC; k++) {
+            if (k < d) {
+                float x[V];
+                ldv<V>(x, slab + (size_t)(e0 + k) * Q + g * V);
+                stv<V>(sc + k * Q + g * V, x);
+            }
         }
+        __syncwarp(mask);
     }
-    __syncwarp(mask);
     float S[DC][V];  // S[k] = qt_{k+1} * ... * qt_{d-1} for k <= d-2
 #pragma unroll
     for (int k = DC - 2; k >= 0; k--) {
@@ -203,19 +210,26 @@ __device__ __forceinline__ void pus_var(const DecodeArgs& A, float* slab, int f,
 }
 
 // Per-group scratch floats: one vector (transform route) or the check's d
-// stored vectors plus two operands (probability route); +4 floats of padding
+// stored vectors plus two operands (probability route; with BULK two buffers
+// of d vectors, filled by bulk copies one check ahead); +4 floats of padding
 // spread the groups over the shared-memory banks.
-template <int Q, int DC, int METHOD>
+template <int Q, int DC, int METHOD, bool BULK = false>
 constexpr int pus_group_scratch() {
-    return (METHOD == kDirect ? (DC + 2) * Q : Q) + 4;
+    return (METHOD == kDirect ? ((BULK ? 2 : 1) * DC + 2) * Q : Q) + 4;
 }
 
 // One frame's whole PUS decode by the calling CTA (all its threads).
-template <int Q, int DC, int DV, int METHOD>
+// BULK (probability route): a group's next check is fetched by a bulk copy
+// into its second buffer while the current one is combined; s_bar holds two
+// mbarriers per group, `phase` the parity of each (per thread, kept across
+// frames), s_fail is set when a wait gave up (the frame then reports -1).
+template <int Q, int DC, int DV, int METHOD, bool BULK = false>
 __device__ __forceinline__ void pus_frame(const DecodeArgs& A, int f, const uint8_t* s_exp, const uint8_t* s_log,
-                                          float* s_scr) {
+                                          float* s_scr, uint64_t* s_bar = nullptr, uint32_t* phase = nullptr,
+                                          int* s_fail = nullptr) {
+    static_assert(!BULK || METHOD == kDirect, "bulk staging is for the probability route");
     constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
-    constexpr int SCR = pus_group_scratch<Q, DC, METHOD>();
+    constexpr int SCR = pus_group_scratch<Q, DC, METHOD, BULK>();
     const int tid = threadIdx.x;
     const int g = tid & (G - 1);
     const int grp = tid / G;
@@ -244,17 +258,48 @@ __device__ __forceinline__ void pus_frame(const DecodeArgs& A, int f, const uint
         else to_deviation<Q>(x, A.c.eh[e], sc, mask, g, s_exp, s_log);
         stv<V>(slab + (size_t)e * Q + g * V, x);
     }
+    if constexpr (BULK) {
+        fence_proxy_async();   // the stores above, before the bulk copies that read them
+        if (tid == 0) *s_fail = 0;
+    }
     __syncthreads();
 
     int t = t0 + 1, ok = 0;
     bool fin = false;
     for (;; t++) {
-        for (int i = grp; i < M; i += ngrp) {
-            if constexpr (METHOD == kDirect) pus_check_direct<Q, DC>(A, slab, f, i, sc, mask, g, s_exp, s_log);
-            else pus_check<Q, DC>(A, slab, f, i, sc, mask, g, s_exp, s_log);
+        if constexpr (BULK) {
+            float* ops = sc;
+            float* buf[2] = {sc + 2 * Q, sc + (2 + DC) * Q};
+            uint64_t* bar = s_bar + 2 * grp;
+            auto issue = [&](int i, int b) {
+                if (g == 0) {
+                    const int e0 = A.c.rowptr[i];
+                    const uint32_t bytes = (uint32_t)(A.c.rowptr[i + 1] - e0) * Q * (uint32_t)sizeof(float);
+                    fence_proxy_async();
+                    bulk_load(buf[b], slab + (size_t)e0 * Q, bytes, bar + b);
+                }
+            };
+            int r = 0;
+            if (grp < M) issue(grp, 0);
+            for (int i = grp; i < M; i += ngrp, r++) {
+                const int b = r & 1;
+                if (i + ngrp < M) {
+                    __syncwarp(mask);   // every lane is done with the other buffer
+                    issue(i + ngrp, b ^ 1);
+                }
+                if (!mbar_wait(bar + b, (*phase >> b) & 1u)) *s_fail = 1;
+                *phase ^= 1u << b;
+                pus_check_direct<Q, DC, true>(A, slab, f, i, buf[b], mask, g, s_exp, s_log, ops);
+            }
+        } else {
+            for (int i = grp; i < M; i += ngrp) {
+                if constexpr (METHOD == kDirect) pus_check_direct<Q, DC>(A, slab, f, i, sc, mask, g, s_exp, s_log);
+                else pus_check<Q, DC>(A, slab, f, i, sc, mask, g, s_exp, s_log);
+            }
         }
         __syncthreads();
         for (int j = grp; j < N; j += ngrp) pus_var<Q, DV, METHOD>(A, slab, f, j, sc, mask, g, s_exp, s_log);
+        if constexpr (BULK) fence_proxy_async();   // the q just stored, before the next pass's bulk copies
         __syncthreads();
         int bad = 0;
         for (int i = tid; i < M; i += blockDim.x) {
@@ -289,30 +334,47 @@ __device__ __forceinline__ void pus_frame(const DecodeArgs& A, int f, const uint
             A.trace[(size_t)f * A.max_iter * N + o] = 255;
     }
     if (tid == 0) {
-        if (!A.fstate || fin) {
-            if (A.iters) A.iters[f] = t;
-            A.conv[f] = (uint8_t)ok;
+        bool bad_wait = false;
+        if constexpr (BULK) bad_wait = *s_fail != 0;
+        if (!A.fstate || fin || bad_wait) {
+            if (A.iters) A.iters[f] = bad_wait ? -1 : t;
+            A.conv[f] = (uint8_t)(ok && !bad_wait);
         }
-        if (A.fstate) A.fstate[f] = fin ? (t | (1 << 30)) : t;
+        if (A.fstate) A.fstate[f] = (fin || bad_wait) ? (t | (1 << 30)) : t;
     }
 }
 
-template <int Q, int DC, int DV, int METHOD>
+// Bulk staging applies to the probability route when a vector is a whole
+// number of 16-byte units (q >= 4), so that every check's run of vectors
+// starts on a 16-byte boundary as the copy engine requires.
+template <int Q, int METHOD>
+constexpr bool pus_bulk_ok() { return METHOD == kDirect && Q >= 4; }
+
+template <int Q, int DC, int DV, int METHOD, bool BULK = false>
 __global__ void __launch_bounds__(kPusThreads) k_pus(const DecodeArgs A) {
+    static_assert(!BULK || pus_bulk_ok<Q, METHOD>(), "bulk staging needs the probability route and q >= 4");
+    constexpr int T = kPusThreads;
+    constexpr int NB = BULK ? 2 * (T / Lay<Q>::G) : 1;
     __shared__ uint8_t s_exp[512];
     __shared__ uint8_t s_log[256];
-    __shared__ int s_frame;
+    __shared__ int s_frame, s_fail;
+    __shared__ __align__(8) uint64_t s_bar[NB];
     extern __shared__ __align__(16) float s_scr[];
     const int tid = threadIdx.x;
     for (int k = tid; k < 512; k += blockDim.x) s_exp[k] = A.c.gexp[k];
     for (int k = tid; k < 256; k += blockDim.x) s_log[k] = A.c.glog[k];
+    if constexpr (BULK) {
+        for (int k = tid; k < 2 * ((int)blockDim.x / Lay<Q>::G); k += blockDim.x) mbar_init(&s_bar[k]);
+        mbar_init_fence();
+    }
+    uint32_t phase = 0;   // parity of the next completion of this group's two mbarriers
     for (;;) {
         __syncthreads();
         if (tid == 0) s_frame = atomicAdd(A.work, 1);
         __syncthreads();
         const int f = s_frame;
         if (f >= A.F) break;
-        pus_frame<Q, DC, DV, METHOD>(A, f, s_exp, s_log, s_scr);
+        pus_frame<Q, DC, DV, METHOD, BULK>(A, f, s_exp, s_log, s_scr, s_bar, &phase, &s_fail);
     }
 }
 

@@ -252,3 +252,19 @@ def test_sus_levels_transform_route_markov_step(torch_cuda, oracle):
         full[lay] = gpu_decode(cd, b.obs, b.channel, b.param, "sus", 30, T=b.T, K=b.K, post=True,
                                check_method="transform", layout=lay)
     _same(full["lanes"], full["thread"], "sus decode, transform route, Markov, levels")
+
+
+def test_pus_bulk_staged_equals_plain_staging(torch_cuda):
+    """Up to 8 frames per SM the PUS kernel fetches each check by bulk copies
+    one check ahead; above that it loads them in place.  Both give the same
+    bits: a 64-frame decode (bulk) against the same frames inside a 2000-frame
+    decode (plain), and the 2000-frame decode against the thread layout."""
+    import torch
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch("gf4_n96_bsc005", frames=2000)
+    cd = gfbp.Code.from_coo(b.code)
+    big = gpu_decode(cd, b.obs, b.channel, b.param, "pus", 60, post=True, layout="lanes")
+    small = gpu_decode(cd, b.obs[:64], b.channel, b.param[:64], "pus", 60, post=True, layout="lanes")
+    _same(small, {k: v[:64] for k, v in big.items()}, "bulk vs plain staging")
+    thr = gpu_decode(cd, b.obs, b.channel, b.param, "pus", 60, post=True, layout="thread")
+    _same(big, thr, "plain staging vs thread layout")
