@@ -77,26 +77,17 @@ __device__ __forceinline__ void stq(float* p, const float (&x)[Q]) {
     }
 }
 
-// U <- U (*) Y, (U (*) Y)[y] = sum_x U[x] Y[x XOR y]: partial p over x = 4p..4p+3
-// in increasing x (one FMA chain), partials added in increasing p.
+// U <- U (*) Y, (U (*) Y)[y] = sum_x U[x] Y[x XOR y]: one FMA chain per output
+// in increasing x (the q outputs are independent chains).
 template <int Q>
 __device__ __forceinline__ void xconv_regs(float (&U)[Q], const float (&Y)[Q]) {
-    constexpr int NP = Q >= 4 ? Q / 4 : 1, XL = Q >= 4 ? 4 : Q;
     float o[Q];
 #pragma unroll
-    for (int p = 0; p < NP; p++) {
-        float t[Q];
+    for (int y = 0; y < Q; y++) o[y] = fmaf(U[0], Y[y], 0.f);
 #pragma unroll
-        for (int y = 0; y < Q; y++) t[y] = fmaf(U[4 * p], Y[(4 * p) ^ y], 0.f);
+    for (int x = 1; x < Q; x++)
 #pragma unroll
-        for (int xl = 1; xl < XL; xl++) {
-            const int x = 4 * p + xl;
-#pragma unroll
-            for (int y = 0; y < Q; y++) t[y] = fmaf(U[x], Y[x ^ y], t[y]);
-        }
-#pragma unroll
-        for (int y = 0; y < Q; y++) o[y] = (p == 0) ? t[y] : o[y] + t[y];
-    }
+        for (int y = 0; y < Q; y++) o[y] = fmaf(U[x], Y[x ^ y], o[y]);
 #pragma unroll
     for (int y = 0; y < Q; y++) U[y] = o[y];
 }

@@ -48,35 +48,22 @@ __device__ __forceinline__ unsigned lanes_mask() {
     }
 }
 
-// out[v] = sum_x sa[x] sb[x XOR y] for y = g*V + v (whole vectors in shared memory).
-// Partial sum p takes x = 4p .. 4p+3 in increasing order (one FMA chain each),
-// and the partials are added in increasing p: the same order for any V <= 4.
+// out[v] = sum_x sa[x] sb[x XOR y] for y = g*V + v (whole vectors in shared memory),
+// one FMA chain per output in increasing x: the same order for any V.
 template <int Q, int V>
 __device__ __forceinline__ void xconv_team(float (&out)[V], const float* sa, const float* sb, int g) {
-    constexpr int NP = Q / 4 > 0 ? Q / 4 : 1;
-    float acc[NP][V];
 #pragma unroll
-    for (int p = 0; p < NP; p++)
-#pragma unroll
-        for (int v = 0; v < V; v++) acc[p][v] = 0.f;
+    for (int v = 0; v < V; v++) out[v] = 0.f;
 #pragma unroll
     for (int xb = 0; xb < Q; xb += V) {
         float a[V], b[V];
         ldv<V>(a, sa + xb);
         ldv<V>(b, sb + (xb ^ (g * V)));
-        const int p = xb / 4;
 #pragma unroll
         for (int xl = 0; xl < V; xl++) {
 #pragma unroll
-            for (int v = 0; v < V; v++) acc[p][v] = fmaf(a[xl], b[xl ^ v], acc[p][v]);
+            for (int v = 0; v < V; v++) out[v] = fmaf(a[xl], b[xl ^ v], out[v]);
         }
-    }
-#pragma unroll
-    for (int v = 0; v < V; v++) {
-        float sum = 0.f;
-#pragma unroll
-        for (int p = 0; p < NP; p++) sum += acc[p][v];
-        out[v] = sum;
     }
 }
 
