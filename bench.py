@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sus-width", type=int, default=0, help="SUS lane teams per frame (0 = automatic)")
     ap.add_argument("--layout", default="auto", choices=["auto", "lanes", "thread"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve", "wht", "paper"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve", "wht", "paper", "fig1"],
                     help="batch: the GF(16) N=1000 benchmark (default); mixed: frames of 12 (q, N) classes in one "
                          "persistent launch; serve: Poisson arrivals to the continuous-batching server")
     ap.add_argument("--duration", type=float, default=6.0, help="serve: seconds per offered load")
@@ -257,6 +257,10 @@ def main():
     if args.workload == "paper":
         from bench_modes import run_paper
         run_paper(args)
+        return
+    if args.workload == "fig1":
+        from bench_modes import run_fig1
+        run_fig1(args)
         return
     import torch
     torch.cuda.set_device(local)

@@ -381,3 +381,70 @@ def run_paper(args):
             "higher_is_better": False, "n_gpus": 1, "config": {"frames": F, "max_iter": max_iter},
             "rows": rows}
     print(json.dumps(line), flush=True)
+
+
+def run_fig1(args):
+    """The statistic of Fig. 1: P = fraction of correctly decided symbols after
+    an iteration, dP = its gain in that iteration; the mean gain of PUS over
+    the mean gain of SUS at equal P (20 bins).  GF(8), N = 3333 symbols (9999
+    bits), rate 1/3 (regular (4,6) stand-in for the KS code), the 2S bit chain
+    as source (3 bits per symbol), block priors on, BSC at Table 1's f = 0.23
+    scaled by --noise-scale (default 0.6, where the stand-in code decodes:
+    see --workload paper).  Both schedules decode the same frames."""
+    import torch
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    torch.cuda.set_device(0)
+    F = args.frames if args.frames != 4096 else 2000
+    max_iter = args.max_iter or 200
+    scale = args.noise_scale if args.noise_scale != 1.0 else 0.6
+    f = 0.23 * scale
+    q, N, p = 8, 3333, 3
+    T = W.bit_chain_symbols(W.MARKOV_2S, 3)
+    code = W.regular_code(q, N, dv=4, dc=6, cfg="paper_rate13_q8")
+    cd = gfbp.Code.from_coo(code)
+    bins = np.linspace(0.0, 1.0, 21)
+    sums = {s: np.zeros(20) for s in ("pus", "sus")}
+    cnts = {s: np.zeros(20) for s in ("pus", "sus")}
+    iters = {s: [] for s in ("pus", "sus")}
+    chunk = 500
+    for c0 in range(0, F, chunk):
+        n = min(chunk, F - c0)
+        rng = W.rng_for("fig1_gf8", "frames", c0)
+        src = W.markov_source(rng.random((n, code.K)), T / T.sum(1, keepdims=True))
+        x = W.encode(code, src)
+        obs = torch.from_numpy(W.bsc(rng, x, p, f)).cuda()
+        xd = torch.from_numpy(x.astype(np.uint8)).cuda()
+        for sched in ("pus", "sus"):
+            out = gfbp.decode(cd, obs, "bsc", f, schedule=sched, max_iter=max_iter, T=T, K=code.K, trace=True)
+            tr = out["trace"]                                           # [n][max_iter][N], 255 after the stop
+            it = out["iters"].long()
+            iters[sched].append(it.cpu().numpy())
+            P = (tr == xd[:, None, :]).float().mean(2)                  # [n][max_iter]
+            # after the stop the decision is frozen at the last iteration's
+            last = torch.gather(P, 1, (it - 1).clamp(min=0)[:, None])
+            t_idx = torch.arange(max_iter, device=P.device)[None, :]
+            P = torch.where(t_idx < it[:, None], P, last)
+            # P before the first iteration: the channel's own decisions
+            P0 = ((torch.from_numpy(np.asarray(obs.cpu().numpy() > 0.5, np.int64)) *
+                   (1 << torch.arange(p))).sum(2).cuda() == xd).float().mean(1)
+            Pall = torch.cat([P0[:, None], P], 1).cpu().numpy()
+            dP = np.diff(Pall, axis=1)
+            Pprev = Pall[:, :-1]
+            live = t_idx.cpu().numpy() < it.cpu().numpy()[:, None]     # iterations that ran
+            b = np.clip(np.digitize(Pprev, bins) - 1, 0, 19)
+            np.add.at(sums[sched], b[live], dP[live])
+            np.add.at(cnts[sched], b[live], 1)
+    rows = []
+    for k in range(20):
+        if cnts["pus"][k] > 0 and cnts["sus"][k] > 0:
+            mp, ms = sums["pus"][k] / cnts["pus"][k], sums["sus"][k] / cnts["sus"][k]
+            rows.append({"P": float((bins[k] + bins[k + 1]) / 2), "dP_pus": float(mp), "dP_sus": float(ms),
+                         "ratio_pus_over_sus": float(mp / ms) if ms != 0 else None,
+                         "iters_in_bin": [int(cnts["pus"][k]), int(cnts["sus"][k])]})
+    ratios = [r["ratio_pus_over_sus"] for r in rows if r["ratio_pus_over_sus"] is not None]
+    line = {"metric": "mean dP(PUS) / mean dP(SUS) at equal P (Fig. 1 statistic)", "workload": "fig1",
+            "unit": "ratio", "value": float(np.median(ratios)) if ratios else None, "n_gpus": 1,
+            "config": {"q": q, "N": N, "rate": "1/3 (regular (4,6))", "source": "2S bits, 3 per symbol",
+                       "channel": f"BSC f={f:.4f} (Table 1 f=0.23 x {scale})", "frames": F, "max_iter": max_iter},
+            "mean_iters": {s: float(np.concatenate(iters[s]).mean()) for s in iters}, "bins": rows}
+    print(json.dumps(line), flush=True)
