@@ -501,6 +501,31 @@ __device__ __forceinline__ void xconv_sm(float (&out)[Lay<Q>::V], const float* s
     }
 }
 
+// out1 = sa (*) sb1 and out2 = sa (*) sb2 (each as xconv_sm) with one read of sa.
+template <int Q>
+__device__ __forceinline__ void xconv_sm2(float (&out1)[Lay<Q>::V], float (&out2)[Lay<Q>::V], const float* sa,
+                                          const float* sb1, const float* sb2, int g) {
+    constexpr int V = Lay<Q>::V;
+    static_assert(V == 2 || V == 4, "direct route needs V in {2, 4}");
+#pragma unroll
+    for (int v = 0; v < V; v++) { out1[v] = 0.f; out2[v] = 0.f; }
+#pragma unroll
+    for (int xb = 0; xb < Q; xb += V) {
+        float a[V], b1[V], b2[V];
+        ldv<V>(a, sa + xb);
+        ldv<V>(b1, sb1 + (xb ^ (g * V)));
+        ldv<V>(b2, sb2 + (xb ^ (g * V)));
+#pragma unroll
+        for (int xl = 0; xl < V; xl++) {
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                out1[v] = fmaf(a[xl], b1[xl ^ v], out1[v]);
+                out2[v] = fmaf(a[xl], b2[xl ^ v], out2[v]);
+            }
+        }
+    }
+}
+
 // r[a] = s[z XOR h a] from the distribution s of the other edges' sum, normalised.
 template <int Q, int NB>
 __device__ __forceinline__ void direct_finish_n(float (&x)[NB][Lay<Q>::V], const int (&h)[NB], const int (&z)[NB],

@@ -123,23 +123,15 @@ __device__ __forceinline__ void pus_check_direct(const DecodeArgs& A, float* sla
             } else if (p_id) {
 #pragma unroll
                 for (int v = 0; v < V; v++) out[0][v] = S[k][v];
+                ldv<V>(P, sc + k * Q + g * V);
+                p_id = false;
             } else {
+                // r_k = P * S_k and the next prefix P * qt_k in one pass over P
                 stv<V>(T0 + g * V, P);
                 stv<V>(T1 + g * V, S[k]);
                 __syncwarp(mask);
-                xconv_sm<Q>(out[0], T0, T1, g);
+                xconv_sm2<Q>(out[0], P, T0, T1, sc + k * Q, g);
                 __syncwarp(mask);
-            }
-            if (k < d - 1) {
-                if (p_id) {
-                    ldv<V>(P, sc + k * Q + g * V);
-                    p_id = false;
-                } else {
-                    stv<V>(T0 + g * V, P);
-                    __syncwarp(mask);
-                    xconv_sm<Q>(P, T0, sc + k * Q, g);
-                    __syncwarp(mask);
-                }
             }
             const int hh[1] = {A.c.eh[e0 + k]}, zz[1] = {z};
             direct_finish_n<Q, 1>(out, hh, zz, 1, T1, mask, g, ex, lg);
