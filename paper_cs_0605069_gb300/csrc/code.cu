@@ -151,18 +151,20 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     }
     std::vector<int2> lpair;
     std::vector<int> lpiece(1, 0);
-    lpair.reserve(E);
+    lpair.reserve(E + N);
     {
         int cur = -1, in_piece = 0;
         for (int j : lorder) {
             const int d = colptr[j + 1] - colptr[j];
-            if (lev[j] != cur || in_piece + d > gfbp::kLevelPiece) {
+            // a column without checks gets one pair (j, 0): only its posterior
+            const int np = d > 0 ? d : 1;
+            if (lev[j] != cur || in_piece + np > gfbp::kLevelPiece) {
                 if (in_piece) lpiece.push_back((int)lpair.size());
                 in_piece = 0;
                 cur = lev[j];
             }
-            for (int k = 0; k < d; k++) lpair.push_back(make_int2(j, k));
-            in_piece += d;
+            for (int k = 0; k < np; k++) lpair.push_back(make_int2(j, k));
+            in_piece += np;
         }
         if (in_piece) lpiece.push_back((int)lpair.size());
     }
@@ -175,7 +177,7 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     const size_t sz[] = {sizeof(int) * (size_t)(M + 1), sizeof(int) * (size_t)(N + 1), sizeof(int) * (size_t)E,
                            sizeof(int) * (size_t)E,       sizeof(int) * (size_t)E,       (size_t)E,
                            512,                           256,                           sizeof(int4) * (size_t)E,
-                           (size_t)N,                     sizeof(int) * (size_t)N,       sizeof(int2) * (size_t)E,
+                           (size_t)N,                     sizeof(int) * (size_t)N,       sizeof(int2) * lpair.size(),
                            sizeof(int) * lpiece.size()};
     static_assert(sizeof(sz) / sizeof(sz[0]) == NA, "one size per array");
     for (int k = 0; k < NA; k++) { off[k] = total; total += align256(sz[k] ? sz[k] : 1); }
@@ -193,7 +195,7 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     std::memcpy(host.data() + off[7], lg, 256);
     std::memcpy(host.data() + off[9], cdep.data(), sz[9]);
     std::memcpy(host.data() + off[10], cpred.data(), sz[10]);
-    if (E) std::memcpy(host.data() + off[11], lpair.data(), sz[11]);
+    if (!lpair.empty()) std::memcpy(host.data() + off[11], lpair.data(), sz[11]);
     std::memcpy(host.data() + off[12], lpiece.data(), sz[12]);
 
     gfbp_code* c = new (std::nothrow) gfbp_code();

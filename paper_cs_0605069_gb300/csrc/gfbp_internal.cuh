@@ -48,7 +48,8 @@ struct CodeDev {
     // columns that share a check with j.  Columns of one level share no check;
     // updating the levels in turn gives the sequential order's values.
     int nlevels, npieces;
-    const int2* lpair;   // [E] (column, slot) pairs, by level, columns increasing
+    const int2* lpair;   // (column, slot) pairs by level, columns increasing; a column
+                         // without checks has the one pair (j, 0)
     const int* lpiece;   // [npieces+1] pair offsets: whole columns of one level, <= kLevelPiece pairs
 };
 

@@ -123,6 +123,7 @@ template <int Q, int DC>
 __device__ __forceinline__ void level_check(const DecodeArgs& A, int f, const float* slab, const uint8_t* zf,
                                             int2 pr, const uint8_t* s_mul, float* row) {
     const int j = pr.x, k = pr.y;
+    if (A.c.colptr[j + 1] == A.c.colptr[j]) return;   // a column without checks
     const int4 in = A.c.cinfo[A.c.colptr[j] + k];
     const int own = in.x - in.y;
     const int dc = in.z & 255;
@@ -173,7 +174,7 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
     const int j = pr.x, k = pr.y;
     const int c0 = A.c.colptr[j];
     const int d = A.c.colptr[j + 1] - c0;
-    const int4 in = A.c.cinfo[c0 + k];
+    const int4 in = d > 0 ? A.c.cinfo[c0 + k] : make_int4(0, 0, 0, 0);
     const int h = (in.z >> 8) & 255;
     const int N = A.c.N;
     float p[Q];
@@ -214,6 +215,7 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
         if (A.post) stq<Q>(A.post + ((size_t)f * N + j) * Q, all);
         if (si >= 0) stq<Q>(A.Qsrc + ((size_t)f * A.K + si) * Q, all);
     }
+    if (d == 0) return;
     normalise_regs<Q>(other);
     if (A.step) stq<Q>(A.msg_io + ((size_t)f * A.c.E + in.x) * Q, other);
     // stored form: qt[y] = q[h^-1 y]

@@ -68,6 +68,11 @@ template <int Q>
 __device__ __forceinline__ void level_tc_check(const DecodeArgs& A, const float* slab, int2 pr, __half* hi_row,
                                                __half* lo_row, float* rs, unsigned mask, int g) {
     constexpr int V = Lay<Q>::V;
+    if (A.c.colptr[pr.x + 1] == A.c.colptr[pr.x]) {   // a column without checks: a zero row
+        const float zero[V] = {};
+        stage_vec<Q>(zero, hi_row, lo_row, rs, mask, g);
+        return;
+    }
     const int4 in = A.c.cinfo[A.c.colptr[pr.x] + pr.y];
     const int own = in.x - in.y;
     const int dc = in.z & 255;
@@ -90,6 +95,7 @@ template <int Q>
 __device__ __forceinline__ void level_tc_finish(const DecodeArgs& A, const uint8_t* zf, int2 pr, float* row,
                                                 unsigned mask, int g, const uint8_t* ex, const uint8_t* lg) {
     constexpr int V = Lay<Q>::V;
+    if (A.c.colptr[pr.x + 1] == A.c.colptr[pr.x]) return;   // a column without checks
     const int4 in = A.c.cinfo[A.c.colptr[pr.x] + pr.y];
     const int h = (in.z >> 8) & 255;
     const int z = zf ? (zf[in.w] & (Q - 1)) : 0;
@@ -110,7 +116,7 @@ __device__ __forceinline__ void level_tc_var(const DecodeArgs& A, int f, uint8_t
     const int j = pr.x, k = pr.y;
     const int c0 = A.c.colptr[j];
     const int d = A.c.colptr[j + 1] - c0;
-    const int4 in = A.c.cinfo[c0 + k];
+    const int4 in = d > 0 ? A.c.cinfo[c0 + k] : make_int4(0, 0, 0, 0);
     const int N = A.c.N;
     const float* r0 = rows0 - (size_t)k * Q;   // row of the column's slot 0
     float p[V];
@@ -134,7 +140,12 @@ __device__ __forceinline__ void level_tc_var(const DecodeArgs& A, int f, uint8_t
     }
     if (k == 0) {
         float r[V], Qj[V];
-        ldv<V>(r, r0 + g * V);
+        if (d > 0) {
+            ldv<V>(r, r0 + g * V);
+        } else {   // no checks: Q_j = p_j
+#pragma unroll
+            for (int v = 0; v < V; v++) r[v] = 1.f;
+        }
 #pragma unroll
         for (int v = 0; v < V; v++) Qj[v] = p[v] * (S[v] * r[v]);
         gnormalise<Q>(Qj, mask);
@@ -145,6 +156,11 @@ __device__ __forceinline__ void level_tc_var(const DecodeArgs& A, int f, uint8_t
             const int si = A.src_index[j];
             if (si >= 0) stv<V>(A.Qsrc + ((size_t)f * A.K + si) * Q + g * V, Qj);
         }
+    }
+    if (d == 0) {   // nothing to store; stage a zero row for the warps' transform
+        const float zero[V] = {};
+        stage_vec<Q>(zero, hi_row, lo_row, rs, mask, g);
+        return;
     }
     float x[V];
 #pragma unroll
@@ -215,6 +231,7 @@ __device__ __forceinline__ void sus_level_tc_frame(const DecodeArgs& A, int f, c
                 __syncthreads();
                 for (int lp = grp; lp < n; lp += NG) {
                     const int2 pr = A.c.lpair[s + lp];
+                    if (A.c.colptr[pr.x + 1] == A.c.colptr[pr.x]) continue;   // no edge to store
                     const int ed = A.c.cinfo[A.c.colptr[pr.x] + pr.y].x;
                     float F[V];
                     ldv<V>(F, rows + (size_t)lp * Q + g * V);

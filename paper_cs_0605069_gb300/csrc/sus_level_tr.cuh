@@ -36,6 +36,7 @@ __device__ __forceinline__ void level_tr_check(const DecodeArgs& A, const float*
                                                const uint8_t* lg) {
     constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
     const int j = pr.x, k = pr.y;
+    if (A.c.colptr[j + 1] == A.c.colptr[j]) return;   // a column without checks
     const int4 in = A.c.cinfo[A.c.colptr[j] + k];
     const int own = in.x - in.y;
     const int dc = in.z & 255;
@@ -70,7 +71,7 @@ __device__ __forceinline__ void level_tr_var(const DecodeArgs& A, int f, float* 
     const int j = pr.x, k = pr.y;
     const int c0 = A.c.colptr[j];
     const int d = A.c.colptr[j + 1] - c0;
-    const int4 in = A.c.cinfo[c0 + k];
+    const int4 in = d > 0 ? A.c.cinfo[c0 + k] : make_int4(0, 0, 0, 0);
     const int N = A.c.N;
     const float* r0 = rows0 - (size_t)k * Q;   // row of the column's slot 0
     float p[V];
@@ -97,7 +98,12 @@ __device__ __forceinline__ void level_tr_var(const DecodeArgs& A, int f, float* 
     if (k == 0) {
         // acc: every row from the last one down (S times row 0, in that order)
         float acc[V], r[V];
-        ldv<V>(r, r0 + g * V);
+        if (d > 0) {
+            ldv<V>(r, r0 + g * V);
+        } else {   // no checks: Q_j = p_j
+#pragma unroll
+            for (int v = 0; v < V; v++) r[v] = 1.f;
+        }
 #pragma unroll
         for (int v = 0; v < V; v++) acc[v] = S[v] * r[v];
         float Qj[V];
@@ -112,6 +118,7 @@ __device__ __forceinline__ void level_tr_var(const DecodeArgs& A, int f, float* 
             if (si >= 0) stv<V>(A.Qsrc + ((size_t)f * A.K + si) * Q + g * V, Qj);
         }
     }
+    if (d == 0) return;
     float x[1][V];
 #pragma unroll
     for (int v = 0; v < V; v++) x[0][v] = p[v] * (pre[v] * S[v]);

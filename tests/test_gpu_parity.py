@@ -43,7 +43,7 @@ def _workload(name, frames, N=None):
 
 
 def _lockstep(torch_cuda, oracle, code, obs, kind, param, schedule, iters, T=None, K=0, atol=LOCKSTEP_ATOL,
-              method="auto"):
+              method="auto", layout="auto"):
     import torch
     from paper_cs_0605069_gb300 import gfbp
     cd = gfbp.Code.from_coo(code)
@@ -60,7 +60,7 @@ def _lockstep(torch_cuda, oracle, code, obs, kind, param, schedule, iters, T=Non
         m = to_dev(msg.astype(np.float32))
         out = gfbp.step(cd, to_dev(obs, torch.float32), m, channel=kind, schedule=schedule, T=T, K=K,
                         prior_in=None if prior is None else to_dev(prior.astype(np.float32)), frame_param=fp,
-                        check_method=method)
+                        check_method=method, layout=layout)
         torch.cuda.synchronize()
         post = out["post"].cpu().numpy()
         dpost = np.abs(post - ref["post"]).max()
@@ -302,3 +302,74 @@ def test_free_running_tensor_route_gf64(torch_cuda, oracle):
     sig = np.array([W.ebn0_to_sigma(db) for db in (1.5, 2.0, 2.5)])[np.arange(F) % 3]
     obs = W.biawgn(rng, x, code.p, sig)
     _free_running(oracle, Batchlike(code, obs, sig, 40), "awgn", "sus", method="tensor")
+
+
+def _code_with_empty_columns(q, seed):
+    """A 6 x 12 H over GF(q) whose columns 5 and 11 meet no check (a symbol the
+    code leaves free: its posterior is its channel likelihood alone)."""
+    from paper_cs_0605069_gb300 import workload as W
+    rng = np.random.default_rng(seed)
+    H = np.zeros((6, 12), np.int64)
+    for j in range(12):
+        if j in (5, 11):
+            continue
+        # column degrees 1 to 3 and row degrees at most 8 keep the code within
+        # the single-team SUS kernel, the lane layout's route for q <= 16
+        rows = rng.choice(6, size=1 + j % 3, replace=False)
+        H[rows, j] = rng.integers(1, q, size=rows.size)
+    for i in range(6):
+        while np.count_nonzero(H[i]) < 2:
+            j = rng.choice([c for c in range(12) if c not in (5, 11) and H[i, c] == 0])
+            H[i, j] = rng.integers(1, q)
+    return W.code_from_dense(H, q), rng
+
+
+@pytest.mark.parametrize("q,method,layout", [
+    (4, "direct", "thread"), (4, "direct", "lanes"), (16, "direct", "thread"),
+    (32, "transform", "thread"), (32, "transform", "lanes"), (16, "tensor", "auto"), (64, "tensor", "auto"),
+])
+@pytest.mark.parametrize("schedule", ["sus", "pus"])
+def test_lockstep_columns_without_checks(torch_cuda, oracle, q, method, layout, schedule):
+    if method == "tensor" and schedule == "pus":
+        pytest.skip("the tensor check method is a SUS route")
+    from paper_cs_0605069_gb300 import workload as W
+    code, rng = _code_with_empty_columns(q, q)
+    F = 5
+    obs = W.bsc(rng, np.zeros((F, code.N), np.int64), code.p, 0.1)
+    atol = TENSOR_ATOL if method == "tensor" else _atol(method, schedule)
+    _lockstep(torch_cuda, oracle, code, obs, "bsc", np.full(F, 0.1), schedule, iters=4, method=method,
+              atol=atol, layout=layout)
+
+
+@pytest.mark.parametrize("q,method", [(4, "direct"), (32, "transform"), (16, "tensor")])
+def test_free_running_columns_without_checks(torch_cuda, oracle, q, method):
+    """Decoding to the end: the free columns' decisions are their channel
+    argmax, and the level kernels agree with the lane kernels bit for bit."""
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    from tests.parity_util import gpu_decode
+    code, rng = _code_with_empty_columns(q, 100 + q)
+    F = 12
+    obs = W.bsc(rng, np.zeros((F, code.N), np.int64), code.p, 0.15)
+    cd = gfbp.Code.from_coo(code)
+    outs = {}
+    for lay in (("auto",) if method == "tensor" else ("lanes", "thread")):
+        outs[lay] = gpu_decode(cd, obs, "bsc", 0.15, "sus", 20, post=True, trace=True, check_method=method,
+                               layout=lay)
+    if method != "tensor":
+        a, b = outs["lanes"], outs["thread"]
+        for k in a:
+            x, y = np.asarray(a[k]), np.asarray(b[k])
+            if x.dtype == np.float32:
+                x, y = x.view(np.uint32), y.view(np.uint32)
+            assert np.array_equal(x, y), f"{k} differs between the lane and level kernels"
+    out = next(iter(outs.values()))
+    # BSC likelihood of each symbol value from the received bits, normalised
+    a = np.arange(q)
+    bits = (a[:, None] >> np.arange(code.p)[None, :]) & 1            # [q, p]
+    for j in (5, 11):
+        rx = obs[:, j, :].astype(np.int64)                            # [F, p]
+        flips = (bits[None, :, :] != rx[:, None, :]).sum(axis=2)      # [F, q]
+        lik = 0.15 ** flips * 0.85 ** (code.p - flips)
+        lik /= lik.sum(axis=1, keepdims=True)
+        np.testing.assert_allclose(out["post"][:, j], lik, atol=1e-6)
+        np.testing.assert_array_equal(out["x_hat"][:, j], (rx << np.arange(code.p)).sum(axis=1))
