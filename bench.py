@@ -33,16 +33,18 @@ WORKLOAD = "gf16_n1000_awgn"
 # reads and writes the single stored slab once per sweep plus the prior (28 q).
 ALG_BYTES_PER_SYMITER = {"pus": 52, "sus": 28}
 # Algorithmic FP32 FMAs per symbol-iteration of the probability-domain check
-# node (q <= 16; d_v = 3, d_c = 6, M/N = 1/2): SUS folds the d_c - 1 other
-# edges of each of a column's 3 checks (4 convolutions of q^2 FMAs each):
-# 12 q^2; PUS runs 3 (d_c - 2) = 12 convolutions per check, M/N checks per
-# symbol: 6 q^2.
-ALG_FMA_PER_SYMITER_Q2 = {"pus": 6, "sus": 12}
+# node (q <= 16; d_v = 3, d_c = 6, M/N = 1/2), convolutions of q^2 FMAs: PUS
+# runs 3 (d_c - 2) = 12 per check, M/N checks per symbol: 6 q^2.  SUS with
+# running partials: d_c - 2 suffixes per check at the sweep start plus, at each
+# of the d_c - 2 inner positions, one for r and one for the prefix: also
+# 3 (d_c - 2) per check, 6 q^2.  SUS folding per visit: d_c - 2 for each of a
+# column's 3 checks, 12 q^2.
+ALG_FMA_PER_SYMITER_Q2 = {"pus": 6, "sus": 6, "sus_fold": 12}
 # FP32 FMA rate: 152 SMs x 4 schedulers x 32 lanes, one FMA (2 flop) per lane
 # per clock, at the sampled SM clock (2070 MHz maximum).
 FP32_LANES = 152 * 4 * 32
 # The kernel of each schedule on the benchmark path (layout AUTO).
-BENCH_KERNEL = {"pus": "k_pus<16,6,3,0,false>", "sus": "k_sus_level<16,8,128>"}
+BENCH_KERNEL = {"pus": "k_pus<16,6,3,0,false>", "sus": "k_sus_level<16,8,64,false>"}
 
 
 def parse():
@@ -59,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sus-width", type=int, default=0, help="SUS lane teams per frame (0 = automatic)")
     ap.add_argument("--layout", default="auto", choices=["auto", "lanes", "thread"])
+    ap.add_argument("--partials", default="auto", choices=["auto", "fold", "running", "running_global"],
+                    help="SUS level kernel: check messages folded per visit or carried as running partials")
     ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve", "wht", "paper", "fig1"],
                     help="batch: the GF(16) N=1000 benchmark (default); mixed: frames of 12 (q, N) classes in one "
                          "persistent launch; serve: Poisson arrivals to the continuous-batching server")
@@ -290,7 +294,7 @@ def main():
             ev = record[s] if record else None
             gfbp.decode(code, obs, "awgn", 0.0, schedule=s, max_iter=max_iter, frame_param=sig,
                         workspace=ws[s], out=outs[s], kernel_events=ev, check_method=args.method,
-                        sus_width=args.sus_width, layout=args.layout)
+                        sus_width=args.sus_width, layout=args.layout, partials=args.partials)
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -340,7 +344,7 @@ def main():
             for s in scheds:
                 gfbp.decode(code, obs_d, "awgn", 0.0, schedule=s, max_iter=max_iter, frame_param=sig_d,
                             workspace=ws[s], out=outs[s], check_method=args.method, sus_width=args.sus_width,
-                            layout=args.layout)
+                            layout=args.layout, partials=args.partials)
                 for k in outs[s]:
                     host_out[s][k].copy_(outs[s][k], non_blocking=True)
 
@@ -380,15 +384,18 @@ def main():
     hbm_gbs = ALG_BYTES_PER_SYMITER[dom] * q * symit_launch / secs / 1e9
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     alu_peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-    alu_tf = 2 * ALG_FMA_PER_SYMITER_Q2[dom] * q * q * symit_launch / secs / 1e12
-    kernel = BENCH_KERNEL[dom] if args.layout == "auto" and args.method == "auto" else None
+    # AUTO folds per visit at the benchmark's 27 frames per SM
+    fma_key = "sus_fold" if dom == "sus" and args.partials in ("auto", "fold") else dom
+    alu_tf = 2 * ALG_FMA_PER_SYMITER_Q2[fma_key] * q * q * symit_launch / secs / 1e12
+    kernel = (BENCH_KERNEL[dom] if args.layout == "auto" and args.method == "auto" and args.partials == "auto"
+              else None)
     traffic = profiled_traffic(kernel, symit_launch) if kernel else None
     hbm = {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
            "peak_source": "measured" if peaks else "fallback",
            "algorithmic_bytes_per_symiter": ALG_BYTES_PER_SYMITER[dom] * q}
     alu = {"achieved": alu_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_tf / alu_peak,
            "peak_source": f"derived: {FP32_LANES} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sampled SM clock)",
-           "algorithmic_flops_per_symiter": 2 * ALG_FMA_PER_SYMITER_Q2[dom] * q * q}
+           "algorithmic_flops_per_symiter": 2 * ALG_FMA_PER_SYMITER_Q2[fma_key] * q * q}
     main, other, bound = (alu, hbm, "alu") if alu["frac"] >= hbm["frac"] else (hbm, alu, "hbm")
     roof = {"bound": bound, **main, "traffic": traffic, "kernel": kernel or f"{dom} ({args.layout}/{args.method})",
             ("hbm_model" if bound == "alu" else "alu_model"): other}
@@ -400,7 +407,7 @@ def main():
             "config": {"workload": WORKLOAD, "q": q, "N": N, "M": b.code.M, "code": "regular (3,6) rate 1/2",
                        "channel": "BI-AWGN, Eb/N0 1.0/1.5/2.0 dB round-robin", "frames_per_gpu": F,
                        "max_iter": max_iter, "schedules": list(scheds), "check_method": args.method,
-                       "layout": args.layout, "sus_width": args.sus_width,
+                       "layout": args.layout, "sus_width": args.sus_width, "sus_partials": args.partials,
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"frames sharded over {world} GPU(s), no collective"},
             "sym_iter_per_s": sum(per[s]["sym_iter_per_s"] for s in scheds) / len(scheds),

@@ -154,6 +154,42 @@ typedef enum {
  */
 typedef enum { GFBP_LAYOUT_AUTO = 0, GFBP_LAYOUT_LANES = 1, GFBP_LAYOUT_THREAD = 2 } gfbp_layout;
 
+/*
+ * How the SUS level kernel (THREAD layout, DIRECT check node, q <= 16)
+ * gathers a check's other messages (Eq. 3) when it visits column j.  When the
+ * sweep reaches j, the check's messages from columns before j already hold
+ * this sweep's values and those from columns after j still hold the values
+ * the sweep started with.
+ *   FOLD     every visit convolves the check's d_c - 1 other messages afresh
+ *            (d_c - 2 convolutions per visit); the lane kernels' arithmetic,
+ *            bit for bit.
+ *   RUNNING  at the start of each sweep the suffix convolutions of every
+ *            check's messages (positions m..d_c-1, m >= 1) are formed at once;
+ *            during the sweep each check keeps the convolution of its messages
+ *            updated so far.  A visit then takes at most one convolution for r
+ *            and one to extend the prefix: about half the arithmetic of FOLD.
+ *            The same r up to the order of FP32 operations.  A frame's partials
+ *            sit in shared memory (E q 4 bytes; a CTA of q/4 threads per pair
+ *            per frame: GF(16) up to about 3,300 edges); where they do not
+ *            fit, FOLD runs instead.
+ *   RUNNING_GLOBAL  the same arithmetic with the partials in global memory
+ *            (a second edge slab, F E q 4 bytes, allocated stream-ordered by
+ *            the call itself; refused by gfbp_decode_noalloc): the same bits
+ *            as RUNNING.
+ *   AUTO     RUNNING for at most two frames per SM, where one frame's
+ *            latency sets the decode time (GF(16), N = 1000: 1.6x faster
+ *            than FOLD at one frame per SM), FOLD above (with several frames
+ *            resident per SM it is faster: 34 ms against 48 ms for 4096
+ *            frames x 20 iterations).
+ * Other kernels ignore the option.
+ */
+typedef enum {
+    GFBP_PARTIALS_AUTO = 0,
+    GFBP_PARTIALS_FOLD = 1,
+    GFBP_PARTIALS_RUNNING = 2,
+    GFBP_PARTIALS_RUNNING_GLOBAL = 3
+} gfbp_sus_partials;
+
 /* Optional inputs and outputs of gfbp_decode / gfbp_step (NULL = defaults). */
 typedef struct {
     const uint8_t* punct;    /* device [N]: 1 = symbol not observed (uniform likelihood) */
@@ -174,6 +210,7 @@ typedef struct {
                                 column still sees the values of the sequential order,
                                 so results are the same bit for bit. */
     int32_t layout;          /* gfbp_layout */
+    int32_t sus_partials;    /* gfbp_sus_partials */
 } gfbp_options;
 
 /*

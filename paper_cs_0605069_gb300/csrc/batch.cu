@@ -100,7 +100,8 @@ __device__ __noinline__ void pus_call(const DecodeArgs& A, int f, const uint8_t*
 template <int Q, int T>
 __device__ __noinline__ void sus_level_call(const DecodeArgs& A, int f, const uint8_t* mul, const uint8_t* div,
                                             float* dyn) {
-    sus_level_frame<Q, 8, T>(A, f, mul, div, dyn, dyn + kLevelPiece * (Q + 1));
+    if (A.sfx) sus_level_frame<Q, 8, T, true>(A, f, mul, div, dyn, dyn + kLevelPiece * (Q + 1));
+    else sus_level_frame<Q, 8, T, false>(A, f, mul, div, dyn, dyn + kLevelPiece * (Q + 1));
 }
 
 template <int Q, int T>

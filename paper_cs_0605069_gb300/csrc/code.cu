@@ -169,16 +169,48 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
         if (in_piece) lpiece.push_back((int)lpair.size());
     }
     const int npieces = (int)lpiece.size() - 1;
+    // The same pairs for the q <= 16 level kernel, reordered inside each piece
+    // by the work the running partial convolutions give them (a convolution
+    // in both steps for a check position 1..d_c-2, none otherwise) so that a
+    // warp's threads take the same branch; .y = slot | (index of the pair in
+    // the column-ordered piece) << 8, which keeps a column's rows adjacent.
+    std::vector<int2> lpair_d(lpair.size());
+    for (int pc = 0; pc < npieces; pc++) {
+        const int s = lpiece[pc], e = lpiece[pc + 1];
+        int o = s;
+        for (int cls = 0; cls < 3; cls++)
+            for (int x = s; x < e; x++) {
+                const int j = lpair[x].x, k = lpair[x].y;
+                int c = 2;   // last position of its check, a check of degree 1, or no check
+                if (colptr[j + 1] > colptr[j]) {
+                    const int4 in = cinfo[colptr[j] + k];
+                    const int t = in.x - in.y, dc = in.z & 255;
+                    if (dc >= 2 && t == 0) c = 1;
+                    else if (t >= 1 && t <= dc - 2) c = 0;
+                }
+                if (c == cls) lpair_d[o++] = make_int2(j, k | ((x - s) << 8));
+            }
+    }
+    // per entry of lpair_d: the slot's cinfo (zeros for a column without
+    // checks) and {column, slot | row index << 8, column degree, 0}
+    std::vector<int4> lrec(2 * lpair_d.size());
+    for (size_t x = 0; x < lpair_d.size(); x++) {
+        const int j = lpair_d[x].x, k = lpair_d[x].y & 255;
+        const int d = colptr[j + 1] - colptr[j];
+        lrec[2 * x] = d > 0 ? cinfo[colptr[j] + k] : make_int4(0, 0, 0, 0);
+        lrec[2 * x + 1] = make_int4(j, lpair_d[x].y, d, 0);
+    }
 
     // one device allocation: rowptr | colptr | ecol | erow | cedge | eh | gexp | glog | cinfo | cdep | cpred |
-    // lpair | lpiece
-    constexpr int NA = 13;
+    // lpair | lpiece | lpair_d | lrec
+    constexpr int NA = 15;
     size_t off[NA], total = 0;
     const size_t sz[] = {sizeof(int) * (size_t)(M + 1), sizeof(int) * (size_t)(N + 1), sizeof(int) * (size_t)E,
                            sizeof(int) * (size_t)E,       sizeof(int) * (size_t)E,       (size_t)E,
                            512,                           256,                           sizeof(int4) * (size_t)E,
                            (size_t)N,                     sizeof(int) * (size_t)N,       sizeof(int2) * lpair.size(),
-                           sizeof(int) * lpiece.size()};
+                           sizeof(int) * lpiece.size(),   sizeof(int2) * lpair_d.size(),
+                           sizeof(int4) * lrec.size()};
     static_assert(sizeof(sz) / sizeof(sz[0]) == NA, "one size per array");
     for (int k = 0; k < NA; k++) { off[k] = total; total += align256(sz[k] ? sz[k] : 1); }
     std::vector<uint8_t> host(total, 0);
@@ -197,6 +229,8 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     std::memcpy(host.data() + off[10], cpred.data(), sz[10]);
     if (!lpair.empty()) std::memcpy(host.data() + off[11], lpair.data(), sz[11]);
     std::memcpy(host.data() + off[12], lpiece.data(), sz[12]);
+    if (!lpair_d.empty()) std::memcpy(host.data() + off[13], lpair_d.data(), sz[13]);
+    if (!lrec.empty()) std::memcpy(host.data() + off[14], lrec.data(), sz[14]);
 
     gfbp_code* c = new (std::nothrow) gfbp_code();
     if (!c) { set_error("gfbp_code_create: out of host memory"); return GFBP_ENOMEM; }
@@ -232,6 +266,8 @@ extern "C" gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t
     d.npieces = npieces;
     d.lpair = reinterpret_cast<const int2*>(base + off[11]);
     d.lpiece = reinterpret_cast<const int*>(base + off[12]);
+    d.lpair_d = reinterpret_cast<const int2*>(base + off[13]);
+    d.lrec = reinterpret_cast<const int4*>(base + off[14]);
     c->poly = poly;
     *out = c;
     return GFBP_OK;

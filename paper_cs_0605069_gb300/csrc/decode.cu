@@ -318,6 +318,11 @@ gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const flo
         set_error("sus_width must be 0, 1, 2, 4 or 8");
         return GFBP_EINVAL;
     }
+    A.partials = opt ? opt->sus_partials : GFBP_PARTIALS_AUTO;
+    if (A.partials < GFBP_PARTIALS_AUTO || A.partials > GFBP_PARTIALS_RUNNING_GLOBAL) {
+        set_error("unknown sus_partials");
+        return GFBP_EINVAL;
+    }
     return GFBP_OK;
 }
 
@@ -378,6 +383,17 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
         own = true;
     }
     if (e == cudaSuccess) e = place_args(A, l, ws, C, step, prior_in, stream);
+    // running partials kept in global memory: a second edge slab of this call's own
+    void* sfx = nullptr;
+    if (e == cudaSuccess && schedule == GFBP_SUS && A.partials == GFBP_PARTIALS_RUNNING_GLOBAL &&
+        A.method == kDirect && A.layout != GFBP_LAYOUT_LANES) {
+        e = cudaMallocAsync(&sfx, sizeof(float) * (size_t)F * (size_t)c.E * c.q, stream);
+        if (e != cudaSuccess) {
+            if (own) cudaFreeAsync(ws, stream);
+            return cuda_fail("partials allocation", e);
+        }
+        A.sfx = static_cast<float*>(sfx);
+    }
     if (C.markov) {
         const size_t q = (size_t)c.q;
         if (!step) {
@@ -397,6 +413,10 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
     if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, stream);
     if (e == cudaSuccess) e = (schedule == GFBP_PUS) ? launch_pus(A, device_sms(), stream) : launch_sus(A, device_sms(), stream);
     if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, stream);
+    if (sfx) {
+        cudaError_t e2 = cudaFreeAsync(sfx, stream);
+        if (e == cudaSuccess) e = e2;
+    }
     if (own) {
         cudaError_t e2 = cudaFreeAsync(ws, stream);
         if (e == cudaSuccess) e = e2;

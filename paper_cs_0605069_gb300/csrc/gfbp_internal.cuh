@@ -51,6 +51,10 @@ struct CodeDev {
     const int2* lpair;   // (column, slot) pairs by level, columns increasing; a column
                          // without checks has the one pair (j, 0)
     const int* lpiece;   // [npieces+1] pair offsets: whole columns of one level, <= kLevelPiece pairs
+    const int2* lpair_d; // the pairs of each piece regrouped for the q <= 16 level kernel:
+                         // (column, slot | index in the piece's column order << 8)
+    const int4* lrec;    // [2 per lpair_d entry]: the slot's cinfo, then
+                         // {column, slot | row index << 8, column degree, 0}
 };
 
 constexpr int kLevelPiece = 128;
@@ -96,6 +100,13 @@ struct DecodeArgs {
     int round_iters;       // resumable decoding: iterations per launch
     int width;             // SUS team kernels: teams per frame (0 = automatic)
     int layout;            // gfbp_layout
+    int partials;          // gfbp_sus_partials as asked
+    // SUS running partial convolutions in global memory (q <= 16 level
+    // kernel, RUNNING_GLOBAL), else NULL: per frame an [E][q] slab; for check
+    // i with edges e0..e0+d-1, slot e0 + m (1 <= m <= d-2) holds the suffix
+    // convolution of the sweep-start messages of positions m..d-1 and slot e0
+    // the prefix of the messages updated so far
+    float* sfx;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -609,6 +620,8 @@ cudaError_t launch_sus_team(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus_wave(const DecodeArgs& A, int width, int num_sms, cudaStream_t s);
 int sus_auto_width(const DecodeArgs& A, int num_sms);
 bool sus_level_eligible(const DecodeArgs& A);
+bool sus_level_sm_eligible(const DecodeArgs& A, int num_sms);
+cudaError_t launch_sus_level_sm(const DecodeArgs& A, int num_sms, cudaStream_t s);
 bool pus_regs_eligible(const DecodeArgs& A);
 cudaError_t launch_sus_level(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus_level_tr(const DecodeArgs& A, int num_sms, cudaStream_t s);

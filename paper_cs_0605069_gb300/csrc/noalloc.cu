@@ -30,6 +30,10 @@ extern "C" gfbp_status gfbp_decode_noalloc(const gfbp_code* code, int32_t n_fram
         gfbp::set_error("gfbp_decode_noalloc: NULL code");
         return GFBP_EINVAL;
     }
+    if (options && options->sus_partials == GFBP_PARTIALS_RUNNING_GLOBAL) {
+        gfbp::set_error("gfbp_decode_noalloc: sus_partials RUNNING_GLOBAL allocates device memory");
+        return GFBP_EINVAL;
+    }
     size_t need = 0;
     gfbp_status st = gfbp_workspace_size(code, n_frames, schedule, prior, 0, &need);
     if (st != GFBP_OK) return st;

@@ -65,6 +65,7 @@ cudaError_t launch_init_q(const DecodeArgs& A, cudaStream_t s) {
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     if (A.method == kTensor) return launch_sus_level_tc(A, num_sms, s);
     if (A.layout != GFBP_LAYOUT_LANES) {
+        if (sus_level_sm_eligible(A, num_sms)) return launch_sus_level_sm(A, num_sms, s);
         if (sus_level_eligible(A)) return launch_sus_level(A, num_sms, s);
         if (A.method == kTransform) return launch_sus_level_tr(A, num_sms, s);
     }

@@ -166,9 +166,81 @@ __device__ __forceinline__ void level_check(const DecodeArgs& A, int f, const fl
     for (int a = 0; a < Q; a++) row[a] = R[a];
 }
 
-// Step 2 for local pair lp: q of (j, k) from the column's other rows, and for
-// slot 0 the posterior Q_j and the hard decision.
+// Step 1 with the running partial convolutions: the check's other messages
+// are the prefix P of those already updated in this sweep (positions before
+// t) and the suffix of those still at their sweep-start values (positions
+// after t), so r is P (*) S[t+1] (one convolution; none at either end).
 template <int Q>
+__device__ __forceinline__ void level_check_run(const DecodeArgs& A, int f, const float* slab, const uint8_t* zf,
+                                                int2 pr, const uint8_t* s_mul, float* row) {
+    const int j = pr.x, k = pr.y;
+    if (A.c.colptr[j + 1] == A.c.colptr[j]) return;   // a column without checks
+    const int4 in = A.c.cinfo[A.c.colptr[j] + k];
+    const int t = in.x - in.y;
+    const int dc = in.z & 255;
+    const int h = (in.z >> 8) & 255;
+    const int z = zf ? (zf[in.w] & (Q - 1)) : 0;
+    const float* D = slab + (size_t)in.y * Q;
+    const float* S = A.sfx + ((size_t)f * A.c.E + in.y) * Q;
+    if (k == 0) prefetch_l1(A.L + ((size_t)f * A.c.N + j) * Q, Q * (int)sizeof(float));   // for step 2
+    float U[Q];
+    if (dc == 1) {
+        // a check of degree 1: the XOR-sum of no other edges is 0
+#pragma unroll
+        for (int i = 0; i < Q; i++) U[i] = i == 0 ? 1.f : 0.f;
+    } else if (t == 0) {
+        ldq<Q>(U, (dc == 2 ? D : S) + Q);   // S[1]; S[d-1] is the message itself
+    } else {
+        ldq<Q>(U, S);   // the prefix
+        if (t < dc - 1) {
+            float Y[Q];
+            ldq<Q>(Y, (t + 1 == dc - 1 ? D : S) + (size_t)(t + 1) * Q);
+            xconv_regs<Q>(U, Y);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; i++) row[i] = U[i];
+    float R[Q];
+#pragma unroll
+    for (int a = 0; a < Q; a++) R[a] = row[(z ^ s_mul[h * Q + a]) & (Q - 1)];
+    normalise_regs<Q>(R);
+#pragma unroll
+    for (int a = 0; a < Q; a++) row[a] = R[a];
+}
+
+// The suffix convolutions of every check from the sweep-start messages:
+// S[d-1] is the last message, S[m] = S[m+1] (*) q~_m down to m = 1; slots
+// 1..d-2 are stored (a thread per check).
+template <int Q, int T>
+__device__ __forceinline__ void level_suffixes(const DecodeArgs& A, int f, const float* slab) {
+    float* sf = A.sfx + (size_t)f * A.c.E * Q;
+    for (int i = threadIdx.x; i < A.c.M; i += T) {
+        const int e0 = A.c.rowptr[i];
+        const int d = A.c.rowptr[i + 1] - e0;
+        if (d < 3) continue;
+        const float* D = slab + (size_t)e0 * Q;
+        prefetch_l1(D, d * Q * (int)sizeof(float));
+        float U[Q], Y[Q];
+        ldq<Q>(U, D + (size_t)(d - 1) * Q);
+        ldq<Q>(Y, D + (size_t)(d - 2) * Q);
+#pragma unroll 1
+        for (int m = d - 2; m >= 1; m--) {
+            float Yn[Q];   // next operand, loaded one convolution ahead
+            if (m > 1) ldq<Q>(Yn, D + (size_t)(m - 1) * Q);
+            xconv_regs<Q>(U, Y);
+            stq<Q>(sf + (size_t)(e0 + m) * Q, U);
+            if (m > 1) {
+#pragma unroll
+                for (int x = 0; x < Q; x++) Y[x] = Yn[x];
+            }
+        }
+    }
+}
+
+// Step 2 for local pair lp: q of (j, k) from the column's other rows, and for
+// slot 0 the posterior Q_j and the hard decision.  RUN: the check's running
+// prefix then takes in the new message.
+template <int Q, bool RUN>
 __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* slab, uint8_t* xh, int2 pr,
                                           const float* rows0, const uint8_t* s_div, float* orow) {
     const int j = pr.x, k = pr.y;
@@ -225,9 +297,23 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
 #pragma unroll
     for (int y = 0; y < Q; y++) qt[y] = orow[s_div[h * Q + y]];
     stq<Q>(slab + (size_t)in.x * Q, qt);
+    if constexpr (RUN) {
+        const int t = in.x - in.y;
+        if (t < (in.z & 255) - 1) {
+            float* P = A.sfx + ((size_t)f * A.c.E + in.y) * Q;
+            if (t == 0) {
+                stq<Q>(P, qt);
+            } else {
+                float U[Q];
+                ldq<Q>(U, P);
+                xconv_regs<Q>(U, qt);
+                stq<Q>(P, U);
+            }
+        }
+    }
 }
 
-template <int Q, int DC, int T>
+template <int Q, int DC, int T, bool RUN>
 __device__ __forceinline__ void sus_level_frame(const DecodeArgs& A, int f, const uint8_t* s_mul,
                                                 const uint8_t* s_div, float* s_row, float* s_orow) {
     constexpr int RS = Q + 1;   // shared row stride (conflict-free column access)
@@ -248,15 +334,27 @@ __device__ __forceinline__ void sus_level_frame(const DecodeArgs& A, int f, cons
     int t = t0 + 1, ok = 0;
     bool fin = false;
     for (;; t++) {
+        if constexpr (RUN) {
+            level_suffixes<Q, T>(A, f, slab);
+            __syncthreads();
+        }
 #pragma unroll 1
         for (int pc = 0; pc < A.c.npieces; pc++) {
             const int pb = A.c.lpiece[pc];
             const int n = A.c.lpiece[pc + 1] - pb;
-            for (int lp = tid; lp < n; lp += T)
-                level_check<Q, DC>(A, f, slab, zf, A.c.lpair[pb + lp], s_mul, s_row + lp * RS);
+            for (int lp = tid; lp < n; lp += T) {
+                const int2 pr = A.c.lpair_d[pb + lp];
+                const int2 jk = make_int2(pr.x, pr.y & 255);
+                float* row = s_row + (pr.y >> 8) * RS;
+                if constexpr (RUN) level_check_run<Q>(A, f, slab, zf, jk, s_mul, row);
+                else level_check<Q, DC>(A, f, slab, zf, jk, s_mul, row);
+            }
             __syncthreads();
-            for (int lp = tid; lp < n; lp += T)
-                level_var<Q>(A, f, slab, xh, A.c.lpair[pb + lp], s_row + lp * RS, s_div, orow);
+            for (int lp = tid; lp < n; lp += T) {
+                const int2 pr = A.c.lpair_d[pb + lp];
+                level_var<Q, RUN>(A, f, slab, xh, make_int2(pr.x, pr.y & 255), s_row + (pr.y >> 8) * RS, s_div,
+                                  orow);
+            }
             __syncthreads();
         }
         int bad = 0;
@@ -299,7 +397,7 @@ __device__ __forceinline__ void sus_level_frame(const DecodeArgs& A, int f, cons
     }
 }
 
-template <int Q, int DC, int T>
+template <int Q, int DC, int T, bool RUN>
 __global__ void __launch_bounds__(T, 640 / T) k_sus_level(const DecodeArgs A) {
     static_assert(T % 32 == 0, "whole warps");
     __shared__ uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a
@@ -315,7 +413,7 @@ __global__ void __launch_bounds__(T, 640 / T) k_sus_level(const DecodeArgs A) {
         __syncthreads();
         const int f = s_f;
         if (f >= A.F) break;
-        sus_level_frame<Q, DC, T>(A, f, s_mul, s_div, s_row, s_orow);
+        sus_level_frame<Q, DC, T, RUN>(A, f, s_mul, s_div, s_row, s_orow);
     }
 }
 

@@ -23,6 +23,7 @@ CHANNEL = {"bsc": 0, "bec": 1, "awgn": 2, "biawgn": 2, "loglik": 3}
 SCHEDULE = {"pus": 0, "sus": 1}
 CHECK_METHOD = {"auto": 0, "transform": 1, "direct": 2, "tensor": 3}
 LAYOUT = {"auto": 0, "lanes": 1, "thread": 2}
+PARTIALS = {"auto": 0, "fold": 1, "running": 2, "running_global": 3}
 
 # Functions declared in include/gfbp.h (the CPU test checks that every one is exported).
 EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info",
@@ -51,7 +52,7 @@ class gfbp_options(C.Structure):
     _fields_ = [("punct", C.c_void_p), ("syndrome", C.c_void_p), ("post", C.c_void_p),
                 ("xhat_trace", C.c_void_p), ("no_early_stop", C.c_int32), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("kernel_events", C.c_void_p * 2), ("check_method", C.c_int32),
-                ("sus_width", C.c_int32), ("layout", C.c_int32)]
+                ("sus_width", C.c_int32), ("layout", C.c_int32), ("sus_partials", C.c_int32)]
 
 
 def lib() -> C.CDLL:
@@ -160,13 +161,15 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
            T=None, K: int = 0, src_pos=None, frame_param=None, punct=None, syndrome=None, post: bool = False,
            trace: bool = False, no_early_stop: bool = False, workspace=None, out=None, stream=None,
            kernel_events=None, check_method: str = "auto", sus_width: int = 0,
-           layout: str = "auto"):
+           layout: str = "auto", partials: str = "auto"):
     """gfbp_decode on CUDA tensors.  obs: float32 [F][N][p] (or [F][N][q] for
     loglik).  Returns dict of device tensors x_hat [F][N] uint8, iters [F]
     int32, converged [F] uint8 (+ post [F][N][q], trace [F][max_iter][N]).
     layout: "auto", "lanes" or "thread" (kernels for q = 4, 8, 16 with the
     direct check node, same results); sus_width: SUS lane teams per frame of
-    the "lanes" layout (0 = automatic)."""
+    the "lanes" layout (0 = automatic); partials: "auto", "fold", "running" or
+    "running_global" (how the SUS level kernel gathers a check's other
+    messages)."""
     import torch
     F = int(obs.shape[0])
     dev = obs.device
@@ -187,6 +190,7 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
     opt.check_method = CHECK_METHOD[check_method]
     opt.sus_width = int(sus_width)
     opt.layout = LAYOUT[layout]
+    opt.sus_partials = PARTIALS[partials]
     if kernel_events is not None:   # (torch.cuda.Event, torch.cuda.Event) timing the schedule kernel alone
         for ev in kernel_events:    # torch creates the CUDA event on its first record
             if not ev.cuda_event:
@@ -202,7 +206,7 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
 
 def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedule: str = "pus", T=None, K: int = 0,
          src_pos=None, prior_in=None, frame_param=None, punct=None, syndrome=None, stream=None,
-         check_method: str = "auto", sus_width: int = 0, layout: str = "auto"):
+         check_method: str = "auto", sus_width: int = 0, layout: str = "auto", partials: str = "auto"):
     """gfbp_step: one iteration from msg (float32 [F][E][q], updated in place).
     Returns dict(msg, post, x_hat, sat, prior_out)."""
     import torch
@@ -218,6 +222,7 @@ def step(code: Code, obs, msg, channel: str = "bsc", param: float = 0.0, schedul
     opt.check_method = CHECK_METHOD[check_method]
     opt.sus_width = int(sus_width)
     opt.layout = LAYOUT[layout]
+    opt.sus_partials = PARTIALS[partials]
     ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
     _ok(lib().gfbp_step(code.handle, F, _ptr(obs), ch, SCHEDULE[schedule], C.byref(pr), _ptr(msg), _ptr(prior_in),
                         _ptr(prior_out), _ptr(post), _ptr(x_hat), _ptr(sat), C.byref(opt), _stream(stream)),
@@ -243,7 +248,7 @@ def wht(x, method: str = "simt", out=None, stream=None):
 def decode_noalloc(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: str = "pus",
                    max_iter: int = 100, T=None, K: int = 0, src_pos=None, frame_param=None, post: bool = False,
                    check_method: str = "auto", out=None, stream=None, sus_width: int = 0,
-                   layout: str = "auto"):
+                   layout: str = "auto", partials: str = "auto"):
     """gfbp_decode_noalloc on CUDA tensors: like decode(), with the library's
     static device scratch instead of a workspace (no device allocation inside
     the library; the outputs here are caller tensors)."""
@@ -261,6 +266,7 @@ def decode_noalloc(code: Code, obs, channel: str = "bsc", param: float = 0.0, sc
     opt.check_method = CHECK_METHOD[check_method]
     opt.sus_width = int(sus_width)
     opt.layout = LAYOUT[layout]
+    opt.sus_partials = PARTIALS[partials]
     ch = gfbp_channel(CHANNEL[channel], float(param), _ptr(frame_param))
     _ok(lib().gfbp_decode_noalloc(code.handle, F, _ptr(obs), ch, SCHEDULE[schedule], C.byref(pr), int(max_iter),
                                   _ptr(out["x_hat"]), _ptr(out["iters"]), _ptr(out["converged"]), C.byref(opt),

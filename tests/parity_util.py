@@ -19,7 +19,7 @@ def to_dev(a, dtype=None):
 
 def gpu_decode(code_dev, obs, channel, param, schedule, max_iter, T=None, K=0, src_pos=None, punct=None,
                syndrome=None, trace=False, post=False, no_early_stop=False, check_method="auto", sus_width=0,
-               layout="auto"):
+               layout="auto", partials="auto"):
     import torch
     from paper_cs_0605069_gb300 import gfbp
     fp = np.asarray(param, np.float32)
@@ -29,7 +29,7 @@ def gpu_decode(code_dev, obs, channel, param, schedule, max_iter, T=None, K=0, s
                       punct=None if punct is None else to_dev(punct),
                       syndrome=None if syndrome is None else to_dev(syndrome), post=post, trace=trace,
                       no_early_stop=no_early_stop, check_method=check_method, sus_width=sus_width,
-                      layout=layout)
+                      layout=layout, partials=partials)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
 

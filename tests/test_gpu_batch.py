@@ -123,8 +123,8 @@ def test_batch_with_both_kernel_families_equals_each_code_alone(env):
     """Items pinned to warp-per-frame variants (team q=4, group transform
     q=64) beside items on the level schedules (q=16, q=256, q=2): the two
     persistent kernels of one run split the frame table between them, and
-    every item still equals gfbp_decode of its code alone (level, team and
-    group transform kernels give the same bits)."""
+    every item still equals gfbp_decode of its code alone in the same kernel
+    (the team item against the lane layout)."""
     torch, gfbp, W = env
     items = _mixed_items(torch, gfbp, W)
     qs = [it["code"].q for it in items]
@@ -135,7 +135,8 @@ def test_batch_with_both_kernel_families_equals_each_code_alone(env):
     outs = b.run()
     torch.cuda.synchronize()
     for it, o in zip(items, outs):
-        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule="sus", max_iter=40)
+        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule="sus", max_iter=40,
+                          layout="lanes" if it["code"].q == 4 else "auto")
         torch.cuda.synchronize()
         for k in ("x_hat", "iters", "converged"):
             assert torch.equal(ref[k], o[k]), (it["code"].q, k)

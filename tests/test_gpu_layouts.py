@@ -1,10 +1,10 @@
 """Kernels that hold or order the work differently must give the same bits.
 
 SUS: the multi-team kernel starts a column once the last earlier column sharing
-a check with it has finished; the level kernel (thread layout) updates the
-columns level by level (one level's columns share no check).  Both give every
-column the operands of the strictly sequential order with the single-team
-kernel's arithmetic.  PUS: the thread layout (a check or a column per thread,
+a check with it has finished; the level kernel (thread layout, check messages
+folded afresh at every visit) updates the columns level by level (one level's
+columns share no check).  Both give every column the operands of the strictly
+sequential order with the single-team kernel's arithmetic.  PUS: the thread layout (a check or a column per thread,
 vectors in registers) runs the lane-group kernel's arithmetic in the same
 order.  So x_hat, iters, converged, posteriors, traces and lock-step messages
 must match the lane kernels bit for bit."""
@@ -39,7 +39,7 @@ def _widths(cd, obs, kind, param, max_iter, widths=(2, 4, 8), levels=True, **kw)
                      **kw)
     runs = [(f"width {w}", dict(layout="lanes", sus_width=w)) for w in widths]
     if levels:
-        runs.append(("levels", dict(layout="thread")))
+        runs.append(("levels", dict(layout="thread", partials="fold")))
     for what, v in runs:
         out = gpu_decode(cd, obs, kind, param, "sus", max_iter, post=True, trace=True, **v, **kw)
         _same(ref, out, what)
@@ -107,7 +107,7 @@ def test_wave_lockstep_step_equals_single_team(torch_cuda, oracle):
     fp = to_dev(np.asarray(b.param, np.float32))
     outs = {}
     for name, v in (("one team", dict(layout="lanes", sus_width=1)), ("width 4", dict(layout="lanes",
-                    sus_width=4)), ("levels", dict(layout="thread"))):
+                    sus_width=4)), ("levels", dict(layout="thread", partials="fold"))):
         m = to_dev(msg0.astype(np.float32))
         o = gfbp.step(cd, to_dev(b.obs, torch.float32), m, channel=b.channel, schedule="sus", T=b.T, K=b.K,
                       prior_in=prior, frame_param=fp, **v)
@@ -268,3 +268,58 @@ def test_pus_bulk_staged_equals_plain_staging(torch_cuda):
     _same(small, {k: v[:64] for k, v in big.items()}, "bulk vs plain staging")
     thr = gpu_decode(cd, b.obs, b.channel, b.param, "pus", 60, post=True, layout="thread")
     _same(big, thr, "plain staging vs thread layout")
+
+
+# SUS with running partial convolutions: the kernel holding a frame's partials
+# in shared memory against the one holding them in the workspace.
+@pytest.mark.parametrize("name,N,frames,max_iter", [
+    ("gf4_n96_bsc005", None, 64, 60),
+    ("gf16_n1000_awgn", None, 20, 60),
+    ("gf8_n2000_markov_bsc", 300, 18, 40),
+    ("gf8_n2000_markov_bec", 300, 18, 40),
+])
+def test_sus_partials_in_shared_memory_equal_global(torch_cuda, name, N, frames, max_iter):
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch(name, frames=frames, N=N)
+    cd = gfbp.Code.from_coo(b.code)
+    kw = dict(T=b.T, K=b.K, post=True, trace=True, layout="thread")
+    ref = gpu_decode(cd, b.obs, b.channel, b.param, "sus", max_iter, partials="running_global", **kw)
+    out = gpu_decode(cd, b.obs, b.channel, b.param, "sus", max_iter, partials="running", **kw)
+    _same(ref, out, "running partials, shared vs global memory")
+    assert ref["iters"].min() >= 1
+
+
+@pytest.mark.parametrize("q,dv,dc,N", [(2, 3, 6, 240), (8, 6, 12, 120), (16, 4, 8, 240), (4, 3, 16, 256)])
+def test_sus_partials_irregular_degrees_and_syndrome(torch_cuda, q, dv, dc, N):
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    code = W.regular_code(q, N, dv=dv, dc=dc, cfg=f"partials_{q}_{dv}_{dc}", encodable=False)
+    rng = np.random.default_rng(q * 31 + dc)
+    F = 12
+    x = rng.integers(0, q, size=(F, code.N))
+    z = code.syndrome(x).astype(np.uint8)
+    obs = W.bsc(rng, x, code.p, 0.04)
+    cd = gfbp.Code.from_coo(code)
+    kw = dict(syndrome=z, post=True, trace=True, layout="thread")
+    ref = gpu_decode(cd, obs, "bsc", 0.04, "sus", 30, partials="running_global", **kw)
+    out = gpu_decode(cd, obs, "bsc", 0.04, "sus", 30, partials="running", **kw)
+    _same(ref, out, f"GF({q}) ({dv},{dc}) running partials, shared vs global memory")
+
+
+def test_sus_partials_lockstep_step_shared_equals_global(torch_cuda, oracle):
+    import torch
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    b = W.make_batch("gf8_n2000_markov_bsc", frames=8, N=300)
+    cd = gfbp.Code.from_coo(b.code)
+    F = b.obs.shape[0]
+    msg0 = oracle.initial_messages(b.code, b.obs, b.channel, b.param, T=b.T, K=b.K)
+    _, pi = oracle.markov(b.T, np.full((1, b.code.q), 1.0 / b.code.q))
+    prior = to_dev(np.broadcast_to(pi, (F, b.K, b.code.q)).astype(np.float32).copy())
+    fp = to_dev(np.asarray(b.param, np.float32))
+    outs = {}
+    for part in ("running", "running_global"):
+        m = to_dev(msg0.astype(np.float32))
+        o = gfbp.step(cd, to_dev(b.obs, torch.float32), m, channel=b.channel, schedule="sus", T=b.T, K=b.K,
+                      prior_in=prior, frame_param=fp, layout="thread", partials=part)
+        torch.cuda.synchronize()
+        outs[part] = {k: x.cpu().numpy() for k, x in o.items() if x is not None}
+    _same(outs["running_global"], outs["running"], "sus step, running partials")

@@ -53,3 +53,14 @@ def test_noalloc_rejects_batches_beyond_the_static_scratch(env):
         gfbp.decode_noalloc(code, big, "awgn", 0.8)
     assert e.value.status == gfbp.GFBP_EINVAL and "static" in str(e.value)
     code.close()
+
+
+def test_noalloc_refuses_partials_that_allocate(env):
+    torch, gfbp, W = env
+    b = W.make_batch("gf16_n1000_awgn", frames=2)
+    code = gfbp.Code.from_coo(b.code)
+    obs = torch.from_numpy(b.obs).cuda()
+    with pytest.raises(gfbp.GfbpError) as e:
+        gfbp.decode_noalloc(code, obs, "awgn", 0.8, schedule="sus", partials="running_global")
+    assert e.value.status == gfbp.GFBP_EINVAL
+    code.close()
