@@ -100,8 +100,9 @@ __device__ __noinline__ void pus_call(const DecodeArgs& A, int f, const uint8_t*
 template <int Q, int T>
 __device__ __noinline__ void sus_level_call(const DecodeArgs& A, int f, const uint8_t* mul, const uint8_t* div,
                                             float* dyn) {
-    if (A.sfx) sus_level_frame<Q, 8, T, true>(A, f, mul, div, dyn, dyn + kLevelPiece * (Q + 1));
-    else sus_level_frame<Q, 8, T, false>(A, f, mul, div, dyn, dyn + kLevelPiece * (Q + 1));
+    // batch items fold per visit (their options are the defaults, and the
+    // running partials' scratch is not allocated for them)
+    sus_level_frame<Q, 8, T, false>(A, f, mul, div, dyn, dyn + kLevelPiece * level_rs<Q>());
 }
 
 template <int Q, int T>
@@ -121,7 +122,7 @@ __device__ __noinline__ void sus_level_tc_call(const DecodeArgs& A, int f, const
 // Dynamic shared memory of a CTA-family variant with T threads.
 template <int Q, int T>
 constexpr size_t level_mixed_bytes() {
-    return sizeof(float) * (Q <= 16 ? (size_t)(kLevelPiece + T) * (Q + 1)
+    return sizeof(float) * (Q <= 16 ? (size_t)(kLevelPiece + T) * level_rs<Q>()
                                     : (size_t)level_tr_sub<Q>() * Q + (size_t)(T / Lay<Q>::G) * (Q + 4));
 }
 constexpr size_t max2(size_t a, size_t b) { return a > b ? a : b; }

@@ -77,6 +77,25 @@ __device__ __forceinline__ void stq(float* p, const float (&x)[Q]) {
     }
 }
 
+// Stride (floats) of the shared r rows and scratch rows of the level kernel:
+// a multiple of 4 floats with (stride / 4) odd for q >= 4, so that eight
+// threads' 16-byte accesses to consecutive rows fall on distinct banks; odd
+// for q = 2 (scalar accesses).
+template <int Q>
+__host__ __device__ constexpr int level_rs() { return Q == 2 ? 3 : (Q == 4 ? 4 : Q + 4); }
+
+// A row of Q floats to / from shared memory at a level_rs-aligned address.
+template <int Q>
+__device__ __forceinline__ void ld_lrow(float (&x)[Q], const float* p) {
+    if constexpr (Q == 2) { x[0] = p[0]; x[1] = p[1]; }
+    else ldq<Q>(x, p);
+}
+template <int Q>
+__device__ __forceinline__ void st_lrow(float* p, const float (&x)[Q]) {
+    if constexpr (Q == 2) { p[0] = x[0]; p[1] = x[1]; }
+    else stq<Q>(p, x);
+}
+
 // U <- U (*) Y, (U (*) Y)[y] = sum_x U[x] Y[x XOR y]: one FMA chain per output
 // in increasing x (the q outputs are independent chains).
 template <int Q>
@@ -156,14 +175,12 @@ __device__ __forceinline__ void level_check(const DecodeArgs& A, int f, const fl
         for (int i = 0; i < Q; i++) U[i] = i == 0 ? 1.f : 0.f;
     }
     // r_ij[a] = s[z XOR h a], normalised
-#pragma unroll
-    for (int i = 0; i < Q; i++) row[i] = U[i];
+    st_lrow<Q>(row, U);
     float R[Q];
 #pragma unroll
-    for (int a = 0; a < Q; a++) R[a] = row[(z ^ s_mul[h * Q + a]) & (Q - 1)];
+    for (int a = 0; a < Q; a++) R[a] = row[z ^ s_mul[h * Q + a]];   // both below Q
     normalise_regs<Q>(R);
-#pragma unroll
-    for (int a = 0; a < Q; a++) row[a] = R[a];
+    st_lrow<Q>(row, R);
 }
 
 // Step 1 with the running partial convolutions: the check's other messages
@@ -198,14 +215,12 @@ __device__ __forceinline__ void level_check_run(const DecodeArgs& A, int f, cons
             xconv_regs<Q>(U, Y);
         }
     }
-#pragma unroll
-    for (int i = 0; i < Q; i++) row[i] = U[i];
+    st_lrow<Q>(row, U);
     float R[Q];
 #pragma unroll
-    for (int a = 0; a < Q; a++) R[a] = row[(z ^ s_mul[h * Q + a]) & (Q - 1)];
+    for (int a = 0; a < Q; a++) R[a] = row[z ^ s_mul[h * Q + a]];   // both below Q
     normalise_regs<Q>(R);
-#pragma unroll
-    for (int a = 0; a < Q; a++) row[a] = R[a];
+    st_lrow<Q>(row, R);
 }
 
 // The suffix convolutions of every check from the sweep-start messages:
@@ -265,15 +280,16 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
     float other[Q], all[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) { other[i] = p[i]; all[i] = p[i]; }
-    const float* r0 = rows0 - (size_t)k * (Q + 1);   // row of the column's slot 0
+    constexpr int RS = level_rs<Q>();
+    const float* r0 = rows0 - (size_t)k * RS;   // row of the column's slot 0
 #pragma unroll 1
     for (int k2 = 0; k2 < d; k2++) {
-        const float* r = r0 + (size_t)k2 * (Q + 1);
+        float r[Q];
+        ld_lrow<Q>(r, r0 + (size_t)k2 * RS);
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            const float v = r[i];
-            all[i] *= v;
-            if (k2 != k) other[i] *= v;
+            all[i] *= r[i];
+            if (k2 != k) other[i] *= r[i];
         }
     }
     if (k == 0) {
@@ -291,8 +307,7 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
     normalise_regs<Q>(other);
     if (A.step) stq<Q>(A.msg_io + ((size_t)f * A.c.E + in.x) * Q, other);
     // stored form: qt[y] = q[h^-1 y]
-#pragma unroll
-    for (int i = 0; i < Q; i++) orow[i] = other[i];
+    st_lrow<Q>(orow, other);
     float qt[Q];
 #pragma unroll
     for (int y = 0; y < Q; y++) qt[y] = orow[s_div[h * Q + y]];
@@ -316,7 +331,7 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
 template <int Q, int DC, int T, bool RUN>
 __device__ __forceinline__ void sus_level_frame(const DecodeArgs& A, int f, const uint8_t* s_mul,
                                                 const uint8_t* s_div, float* s_row, float* s_orow) {
-    constexpr int RS = Q + 1;   // shared row stride (conflict-free column access)
+    constexpr int RS = level_rs<Q>();
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int M = A.c.M, N = A.c.N;
@@ -402,8 +417,8 @@ __global__ void __launch_bounds__(T, 640 / T) k_sus_level(const DecodeArgs A) {
     static_assert(T % 32 == 0, "whole warps");
     __shared__ uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a
     __shared__ uint8_t s_div[Q * Q];   // s_div[h*Q + b] = h^-1 b
-    __shared__ float s_row[kLevelPiece * (Q + 1)];
-    __shared__ float s_orow[T * (Q + 1)];
+    __shared__ __align__(16) float s_row[kLevelPiece * level_rs<Q>()];
+    __shared__ __align__(16) float s_orow[T * level_rs<Q>()];
     __shared__ int s_f;
     const int tid = threadIdx.x;
     team_tables<Q>(A.c.gexp, A.c.glog, s_mul, s_div, tid, T);
