@@ -70,6 +70,30 @@ gfbp_status gfbp_code_create(int32_t q, int32_t M, int32_t N, int64_t nnz, const
 /* Release a code (synchronous; no decode using it may still be in flight). */
 void gfbp_code_destroy(gfbp_code* code);
 
+/*
+ * The SUS level schedule that gfbp_code_create builds for H, computed on the
+ * host alone (no device needed; for inspection and tests).  Column j's level
+ * is 0 when it shares no check with an earlier column, else 1 + the highest
+ * level of those columns, so the columns of one level share no check and
+ * updating the levels in turn, a level's columns at once, gives every column
+ * the operands of the sequential order of Sec. 2.  The levels are cut into
+ * pieces: runs of whole columns of one level (columns increasing), at most
+ * 128 (column, slot) pairs each, a column without checks counting as one
+ * pair (slot 0).  Inside a piece the pairs are listed in the order the q <= 16
+ * level kernel takes them: first those at an inner position of their check
+ * (1..d_c-2), then those at position 0, then the rest; pair_row is the pair's
+ * index in the piece's column order (a column's slots have consecutive rows).
+ *   q, M, N, nnz, row, col, val  as gfbp_code_create (same validation, errors).
+ *   level      host [N] out.
+ *   n_levels   out: 1 + the highest level.
+ *   piece_ptr  host [nnz + N + 1] out: pair offsets of the pieces; n_pieces + 1 written.
+ *   pair_col, pair_slot, pair_row  host [nnz + N] out; n_pairs written.
+ */
+gfbp_status gfbp_level_schedule(int32_t q, int32_t M, int32_t N, int64_t nnz, const int32_t* row, const int32_t* col,
+                                const int32_t* val, int32_t* level, int32_t* n_levels, int32_t* piece_ptr,
+                                int32_t* n_pieces, int32_t* pair_col, int32_t* pair_slot, int32_t* pair_row,
+                                int32_t* n_pairs);
+
 /* Sizes of a code; any output pointer may be NULL. */
 gfbp_status gfbp_code_info(const gfbp_code* code, int32_t* q, int32_t* M, int32_t* N, int64_t* E,
                            int32_t* max_row_degree, int32_t* max_col_degree);

@@ -26,7 +26,7 @@ LAYOUT = {"auto": 0, "lanes": 1, "thread": 2}
 PARTIALS = {"auto": 0, "fold": 1, "running": 2, "running_global": 3}
 
 # Functions declared in include/gfbp.h (the CPU test checks that every one is exported).
-EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info",
+EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info", "gfbp_level_schedule",
            "gfbp_workspace_size", "gfbp_decode", "gfbp_step", "gfbp_decode_noalloc",
            "gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_batch_set_variants",
            "gfbp_batch_destroy", "gfbp_autotune", "gfbp_wht",
@@ -67,6 +67,8 @@ def lib() -> C.CDLL:
             L.gfbp_last_error.restype = C.c_char_p
             L.gfbp_last_error.argtypes = []
             L.gfbp_code_create.argtypes = [i32, i32, i32, i64, P, P, P, u32, C.POINTER(C.c_void_p)]
+            L.gfbp_level_schedule.argtypes = [i32, i32, i32, i64, P, P, P, P, C.POINTER(i32), P, C.POINTER(i32), P,
+                                              P, P, C.POINTER(i32)]
             L.gfbp_code_destroy.argtypes = [P]
             L.gfbp_code_destroy.restype = None
             L.gfbp_code_info.argtypes = [P] + [C.POINTER(i32)] * 3 + [C.POINTER(i64)] + [C.POINTER(i32)] * 2
@@ -127,6 +129,28 @@ class Code:
             self.close()
         except Exception:
             pass
+
+
+def level_schedule(code) -> dict:
+    """gfbp_level_schedule (host only) for an object with q, M, N, rows, cols,
+    vals: the SUS level of every column, the pieces (pair offsets) and the
+    pairs (column, slot, row index in the piece's column order) in the order
+    the level kernel takes them."""
+    r = np.ascontiguousarray(code.rows, dtype=np.int32)
+    c = np.ascontiguousarray(code.cols, dtype=np.int32)
+    v = np.ascontiguousarray(code.vals, dtype=np.int32)
+    cap = int(r.size) + int(code.N)
+    level = np.empty(int(code.N), np.int32)
+    piece_ptr = np.empty(cap + 1, np.int32)
+    pair_col, pair_slot, pair_row = (np.empty(cap, np.int32) for _ in range(3))
+    nl, npc, npr = C.c_int32(), C.c_int32(), C.c_int32()
+    _ok(lib().gfbp_level_schedule(int(code.q), int(code.M), int(code.N), int(r.size), r.ctypes.data, c.ctypes.data,
+                                  v.ctypes.data, level.ctypes.data, C.byref(nl), piece_ptr.ctypes.data, C.byref(npc),
+                                  pair_col.ctypes.data, pair_slot.ctypes.data, pair_row.ctypes.data, C.byref(npr)),
+        "gfbp_level_schedule")
+    n = npr.value
+    return dict(level=level, n_levels=nl.value, piece_ptr=piece_ptr[:npc.value + 1].copy(),
+                pair_col=pair_col[:n].copy(), pair_slot=pair_slot[:n].copy(), pair_row=pair_row[:n].copy())
 
 
 def _ptr(t) -> int | None:
