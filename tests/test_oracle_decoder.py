@@ -72,6 +72,28 @@ def test_tree_codes_reach_exact_marginals(oracle, q, N, schedule, seed):
     np.testing.assert_allclose(out["post"][0], want, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("q,N", [(4, 7), (8, 5)])
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_tree_codes_bit_erasures_reach_exact_marginals(oracle, q, N, schedule):
+    """BEC with bits erased at random (exact-zero likelihoods for every symbol
+    that disagrees with a received bit): on a cycle-free graph BP still
+    reaches the exact marginals of the words consistent with the received
+    bits and H x = z, z the sent word's syndrome."""
+    rng = np.random.default_rng(7 * q + N)
+    code = random_tree_code(rng, N, q)
+    p = q.bit_length() - 1
+    x = rng.integers(0, q, size=N)
+    z = np.asarray(_gf.syndrome(code.rows, code.cols, code.vals, code.M, x, q), np.int64)
+    bits = ((x[:, None] >> np.arange(p)[None, :]) & 1).astype(np.float32)
+    bits[rng.random(bits.shape) < 0.5] = 2.0   # erased
+    L = oracle.channel(q, "bec", 0.5, bits)
+    assert np.all(L[np.arange(N), x] > 0)       # the sent word stays possible
+    want = exact_marginals(code, L, z)
+    out = oracle.decode(code, bits[None], "bec", 0.5, schedule, max_iter=N + code.M + 2,
+                        syn=z[None].astype(np.uint8), early_stop=False, post=True)
+    np.testing.assert_allclose(out["post"][0], want, rtol=0, atol=1e-12)
+
+
 def chain_code(N, q, rng):
     rows = np.repeat(np.arange(N - 1), 2)
     cols = np.stack([np.arange(N - 1), np.arange(1, N)], 1).ravel()
