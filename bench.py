@@ -44,7 +44,7 @@ ALG_FMA_PER_SYMITER_Q2 = {"pus": 6, "sus": 6, "sus_fold": 12}
 # per clock, at the sampled SM clock (2070 MHz maximum).
 FP32_LANES = 152 * 4 * 32
 # The kernel of each schedule on the benchmark path (layout AUTO).
-BENCH_KERNEL = {"pus": "k_pus<16,6,3,0,false>", "sus": "k_sus_level<16,8,64,false>"}
+BENCH_KERNEL = {"pus": "k_pus_regs<16,128>", "sus": "k_sus_level<16,8,64,false>"}
 
 
 def parse():

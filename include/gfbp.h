@@ -170,8 +170,9 @@ typedef enum {
  *           the highest level of the earlier columns sharing a check with j;
  *           one level's columns share no check) and a level's (column, check)
  *           pairs run at once, a thread each.
- *   AUTO    THREAD for SUS, LANES for PUS (the faster of the two on the
- *           GF(16) N = 1000 benchmark batch).
+ *   AUTO    THREAD for SUS; for PUS THREAD at q >= 8 (its vectors move by
+ *           256-bit accesses; 10-23% faster than LANES on GF(16), N = 1000),
+ *           LANES below.
  * SUS with the TRANSFORM check node (any q) also runs by levels unless LANES
  * is asked for: a lane group per (column, check) pair instead of per frame,
  * the same bits as the lane kernel.
@@ -200,10 +201,10 @@ typedef enum { GFBP_LAYOUT_AUTO = 0, GFBP_LAYOUT_LANES = 1, GFBP_LAYOUT_THREAD =
  *            (a second edge slab, F E q 4 bytes, allocated stream-ordered by
  *            the call itself; refused by gfbp_decode_noalloc): the same bits
  *            as RUNNING.
- *   AUTO     RUNNING for at most two frames per SM, where one frame's
- *            latency sets the decode time (GF(16), N = 1000: 1.6x faster
+ *   AUTO     RUNNING for at most one frame per SM, where one frame's
+ *            latency sets the decode time (GF(16), N = 1000: 1.34x faster
  *            than FOLD at one frame per SM), FOLD above (with several frames
- *            resident per SM it is faster: 34 ms against 48 ms for 4096
+ *            resident per SM it is faster: 28 ms against 48 ms for 4096
  *            frames x 20 iterations).
  * Other kernels ignore the option.
  */

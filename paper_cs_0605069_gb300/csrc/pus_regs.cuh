@@ -91,12 +91,12 @@ __device__ __forceinline__ void pus_check_regs(const DecodeArgs& A, float* slab,
     // S_k = qt_{k+1} * ... * qt_{d-1} for k = d-2 .. 0
     if (d >= 2) {
         float S[Q];
-        ldq<Q>(S, D + (size_t)(d - 1) * Q);
+        ldq_g<Q>(S, D + (size_t)(d - 1) * Q);
         st_row<Q>(suf + (d - 2) * rstride, S);
 #pragma unroll 1
         for (int k = d - 3; k >= 0; k--) {
             float X[Q], S2[Q];
-            ldq<Q>(X, D + (size_t)(k + 1) * Q);
+            ldq_g<Q>(X, D + (size_t)(k + 1) * Q);
             xconv_chain<Q>(S2, S, X);
 #pragma unroll
             for (int y = 0; y < Q; y++) S[y] = S2[y];
@@ -120,7 +120,7 @@ __device__ __forceinline__ void pus_check_regs(const DecodeArgs& A, float* slab,
         }
         if (k < d - 1) {
             float X[Q];
-            ldq<Q>(X, D + (size_t)k * Q);   // qt_k, read before r_k replaces it below
+            ldq_g<Q>(X, D + (size_t)k * Q);   // qt_k, read before r_k replaces it below
             if (p_id) {
 #pragma unroll
                 for (int y = 0; y < Q; y++) P[y] = X[y];
@@ -139,7 +139,7 @@ __device__ __forceinline__ void pus_check_regs(const DecodeArgs& A, float* slab,
 #pragma unroll
         for (int a = 0; a < Q; a++) R[a] = row[(z ^ s_mul[h * Q + a]) & (Q - 1)];
         gnormalise_regs<Q>(R);
-        stq<Q>(slab + (size_t)(e0 + k) * Q, R);
+        stq_g<Q>(slab + (size_t)(e0 + k) * Q, R);
     }
 }
 
@@ -153,7 +153,7 @@ __device__ __forceinline__ void pus_var_regs(const DecodeArgs& A, float* slab, i
     const int N = A.c.N;
     for (int k = 0; k < d; k++) prefetch_l1(slab + (size_t)A.c.cedge[c0 + k] * Q, Q * (int)sizeof(float));
     float p[Q];
-    ldgq<Q>(p, A.L + ((size_t)f * N + j) * Q);
+    ldq_g<Q, true>(p, A.L + ((size_t)f * N + j) * Q);
     int si = -1;
     if (A.markov) {
         si = A.src_index[j];
@@ -173,7 +173,7 @@ __device__ __forceinline__ void pus_var_regs(const DecodeArgs& A, float* slab, i
 #pragma unroll 1
     for (int k = d - 1; k >= 0; k--) {
         float R[Q];
-        ldq<Q>(R, slab + (size_t)A.c.cedge[c0 + k] * Q);
+        ldq_g<Q>(R, slab + (size_t)A.c.cedge[c0 + k] * Q);
         st_row<Q>(rr + k * rstride, R);
 #pragma unroll
         for (int i = 0; i < Q; i++) acc[i] *= R[i];
@@ -223,7 +223,7 @@ __device__ __forceinline__ void pus_var_regs(const DecodeArgs& A, float* slab, i
         float qt[Q];
 #pragma unroll
         for (int y = 0; y < Q; y++) qt[y] = row[s_div[h * Q + y]];
-        stq<Q>(slab + (size_t)e * Q, qt);
+        stq_g<Q>(slab + (size_t)e * Q, qt);
     }
 }
 

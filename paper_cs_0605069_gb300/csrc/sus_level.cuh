@@ -59,6 +59,33 @@ __device__ __forceinline__ void ldgq(float (&x)[Q], const float* p) {
     }
 }
 
+// A q-vector from global memory by 256-bit loads (one 32-byte sector each;
+// p 32-byte aligned) for q >= 8, else as ldq.  NC: through the read-only
+// path (data the kernel does not write).
+template <int Q, bool NC = false>
+__device__ __forceinline__ void ldq_g(float (&x)[Q], const float* p) {
+    if constexpr (Q >= 8) {
+#pragma unroll
+        for (int i = 0; i < Q; i += 8) {
+            if constexpr (NC)
+                asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=f"(x[i]), "=f"(x[i + 1]), "=f"(x[i + 2]), "=f"(x[i + 3]), "=f"(x[i + 4]),
+                               "=f"(x[i + 5]), "=f"(x[i + 6]), "=f"(x[i + 7])
+                             : "l"(p + i));
+            else
+                asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=f"(x[i]), "=f"(x[i + 1]), "=f"(x[i + 2]), "=f"(x[i + 3]), "=f"(x[i + 4]),
+                               "=f"(x[i + 5]), "=f"(x[i + 6]), "=f"(x[i + 7])
+                             : "l"(p + i)
+                             : "memory");
+        }
+    } else if constexpr (NC) {
+        ldgq<Q>(x, p);
+    } else {
+        ldq<Q>(x, p);
+    }
+}
+
 // Non-binding L1 prefetch of the 128-byte lines covering [p, p + bytes).
 __device__ __forceinline__ void prefetch_l1(const void* p, int bytes) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)127;
@@ -74,6 +101,21 @@ __device__ __forceinline__ void stq(float* p, const float (&x)[Q]) {
 #pragma unroll
         for (int i = 0; i < Q; i += 4)
             *reinterpret_cast<float4*>(p + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+    }
+}
+
+// A q-vector to global memory by 256-bit stores for q >= 8 (p 32-byte
+// aligned), else as stq.
+template <int Q>
+__device__ __forceinline__ void stq_g(float* p, const float (&x)[Q]) {
+    if constexpr (Q >= 8) {
+#pragma unroll
+        for (int i = 0; i < Q; i += 8)
+            asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p + i), "f"(x[i]), "f"(x[i + 1]),
+                         "f"(x[i + 2]), "f"(x[i + 3]), "f"(x[i + 4]), "f"(x[i + 5]), "f"(x[i + 6]), "f"(x[i + 7])
+                         : "memory");
+    } else {
+        stq<Q>(p, x);
     }
 }
 
@@ -155,14 +197,14 @@ __device__ __forceinline__ void level_check(const DecodeArgs& A, int f, const fl
     if (k == 0) prefetch_l1(A.L + ((size_t)f * A.c.N + j) * Q, Q * (int)sizeof(float));   // for step 2
     float U[Q];
     if (dc > 1) {
-        ldq<Q>(U, D + (0 < own ? 0 : 1) * Q);
+        ldq_g<Q>(U, D + (0 < own ? 0 : 1) * Q);
         float Y[Q];
-        if (dc > 2) ldq<Q>(Y, D + (1 < own ? 1 : 2) * Q);
+        if (dc > 2) ldq_g<Q>(Y, D + (1 < own ? 1 : 2) * Q);
 #pragma unroll 1
         for (int n = 1; n < dc - 1; n++) {
             float Yn[Q];   // next operand, loaded one convolution ahead
             const bool more = n + 1 < dc - 1;
-            if (more) ldq<Q>(Yn, D + (n + 1 < own ? n + 1 : n + 2) * Q);
+            if (more) ldq_g<Q>(Yn, D + (n + 1 < own ? n + 1 : n + 2) * Q);
             xconv_regs<Q>(U, Y);
             if (more) {
 #pragma unroll
@@ -206,12 +248,12 @@ __device__ __forceinline__ void level_check_run(const DecodeArgs& A, int f, cons
 #pragma unroll
         for (int i = 0; i < Q; i++) U[i] = i == 0 ? 1.f : 0.f;
     } else if (t == 0) {
-        ldq<Q>(U, (dc == 2 ? D : S) + Q);   // S[1]; S[d-1] is the message itself
+        ldq_g<Q>(U, (dc == 2 ? D : S) + Q);   // S[1]; S[d-1] is the message itself
     } else {
-        ldq<Q>(U, S);   // the prefix
+        ldq_g<Q>(U, S);   // the prefix
         if (t < dc - 1) {
             float Y[Q];
-            ldq<Q>(Y, (t + 1 == dc - 1 ? D : S) + (size_t)(t + 1) * Q);
+            ldq_g<Q>(Y, (t + 1 == dc - 1 ? D : S) + (size_t)(t + 1) * Q);
             xconv_regs<Q>(U, Y);
         }
     }
@@ -236,14 +278,14 @@ __device__ __forceinline__ void level_suffixes(const DecodeArgs& A, int f, const
         const float* D = slab + (size_t)e0 * Q;
         prefetch_l1(D, d * Q * (int)sizeof(float));
         float U[Q], Y[Q];
-        ldq<Q>(U, D + (size_t)(d - 1) * Q);
-        ldq<Q>(Y, D + (size_t)(d - 2) * Q);
+        ldq_g<Q>(U, D + (size_t)(d - 1) * Q);
+        ldq_g<Q>(Y, D + (size_t)(d - 2) * Q);
 #pragma unroll 1
         for (int m = d - 2; m >= 1; m--) {
             float Yn[Q];   // next operand, loaded one convolution ahead
-            if (m > 1) ldq<Q>(Yn, D + (size_t)(m - 1) * Q);
+            if (m > 1) ldq_g<Q>(Yn, D + (size_t)(m - 1) * Q);
             xconv_regs<Q>(U, Y);
-            stq<Q>(sf + (size_t)(e0 + m) * Q, U);
+            stq_g<Q>(sf + (size_t)(e0 + m) * Q, U);
             if (m > 1) {
 #pragma unroll
                 for (int x = 0; x < Q; x++) Y[x] = Yn[x];
@@ -265,7 +307,7 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
     const int h = (in.z >> 8) & 255;
     const int N = A.c.N;
     float p[Q];
-    ldgq<Q>(p, A.L + ((size_t)f * N + j) * Q);
+    ldq_g<Q, true>(p, A.L + ((size_t)f * N + j) * Q);
     int si = -1;
     if (A.markov) {
         si = A.src_index[j];
@@ -311,18 +353,18 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
     float qt[Q];
 #pragma unroll
     for (int y = 0; y < Q; y++) qt[y] = orow[s_div[h * Q + y]];
-    stq<Q>(slab + (size_t)in.x * Q, qt);
+    stq_g<Q>(slab + (size_t)in.x * Q, qt);
     if constexpr (RUN) {
         const int t = in.x - in.y;
         if (t < (in.z & 255) - 1) {
             float* P = A.sfx + ((size_t)f * A.c.E + in.y) * Q;
             if (t == 0) {
-                stq<Q>(P, qt);
+                stq_g<Q>(P, qt);
             } else {
                 float U[Q];
-                ldq<Q>(U, P);
+                ldq_g<Q>(U, P);
                 xconv_regs<Q>(U, qt);
-                stq<Q>(P, U);
+                stq_g<Q>(P, U);
             }
         }
     }

@@ -52,15 +52,15 @@ bool fits(const DecodeArgs& A) {
 
 }  // namespace
 
-// RUNNING asks for it; AUTO takes it for at most two frames per SM, where a
+// RUNNING asks for it; AUTO takes it for at most one frame per SM, where a
 // frame's latency sets the decode time (GF(16), N = 1000, 20 iterations: 152
-// frames 1.78 ms against 2.85 ms with the folding kernel, 304 frames 3.56
-// against 3.73; from 760 frames on the folding kernel, with several frames
-// resident per SM, is faster: 6.58 against 8.91 ms).
+// frames 1.78 ms against 2.39 ms with the folding kernel; from 304 frames on
+// the folding kernel, with several frames resident per SM, is faster: 3.21
+// against 3.56 ms, and 28.4 against 48.0 ms for 4096 frames).
 bool sus_level_sm_eligible(const DecodeArgs& A, int num_sms) {
     if (A.method != kDirect) return false;
     const bool want = A.partials == GFBP_PARTIALS_RUNNING ||
-                      (A.partials == GFBP_PARTIALS_AUTO && (long long)A.F <= 2LL * num_sms);
+                      (A.partials == GFBP_PARTIALS_AUTO && (long long)A.F <= (long long)num_sms);
     if (!want) return false;
     switch (A.c.q) {
     case 2: return fits<2>(A);
