@@ -137,7 +137,7 @@ __device__ __forceinline__ void pus_check_regs(const DecodeArgs& A, float* slab,
         st_row<Q>(row, out);
         float R[Q];
 #pragma unroll
-        for (int a = 0; a < Q; a++) R[a] = row[(z ^ s_mul[h * Q + a]) & (Q - 1)];
+        for (int a = 0; a < Q; a++) R[a] = row[z ^ s_mul[h * Q + a]];   // both below Q
         gnormalise_regs<Q>(R);
         stq_g<Q>(slab + (size_t)(e0 + k) * Q, R);
     }
