@@ -205,7 +205,10 @@ typedef enum { GFBP_LAYOUT_AUTO = 0, GFBP_LAYOUT_LANES = 1, GFBP_LAYOUT_THREAD =
  *            latency sets the decode time (GF(16), N = 1000: 1.34x faster
  *            than FOLD at one frame per SM), FOLD above (with several frames
  *            resident per SM it is faster: 28 ms against 48 ms for 4096
- *            frames x 20 iterations).
+ *            frames x 20 iterations).  The choice follows the frame count, so
+ *            a frame's posteriors can differ in the last bits between a call
+ *            with few frames and one with many; FOLD or RUNNING fix the
+ *            kernel and with it the bits.
  * Other kernels ignore the option.
  */
 typedef enum {

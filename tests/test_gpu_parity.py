@@ -241,16 +241,20 @@ def test_empty_batch_and_errors(torch_cuda):
         gfbp.decode(cd, to_dev(b.obs), "bsc", 0.05, T=np.eye(4), K=0)
 
 
-@pytest.mark.parametrize("schedule", ["pus", "sus"])
-def test_single_frame_and_large_batch_agree(torch_cuda, schedule):
-    """A frame decodes to the same bits alone and inside a batch (frames are
-    independent; the persistent kernels take them in any order)."""
+@pytest.mark.parametrize("schedule,partials,frames", [("pus", "auto", 300), ("sus", "fold", 300),
+                                                      ("sus", "running", 120)])
+def test_single_frame_and_large_batch_agree(torch_cuda, schedule, partials, frames):
+    """A frame decodes to the same bits alone and inside a batch run by the
+    same kernel (frames are independent; the persistent kernels take them in
+    any order).  SUS with AUTO partials picks its kernel by the frame count,
+    so each SUS kernel is pinned here."""
     from paper_cs_0605069_gb300 import gfbp
-    b = _workload("gf16_n1000_awgn", 300)
+    b = _workload("gf16_n1000_awgn", frames)
     cd = gfbp.Code.from_coo(b.code)
-    full = gpu_decode(cd, b.obs, "awgn", b.param, schedule, 50, post=True)
-    for f in (0, 1, 157, 299):
-        one = gpu_decode(cd, b.obs[f:f + 1], "awgn", b.param[f:f + 1], schedule, 50, post=True)
+    full = gpu_decode(cd, b.obs, "awgn", b.param, schedule, 50, post=True, partials=partials)
+    for f in (0, 1, frames // 2 + 7, frames - 1):
+        one = gpu_decode(cd, b.obs[f:f + 1], "awgn", b.param[f:f + 1], schedule, 50, post=True,
+                         partials=partials)
         assert one["iters"][0] == full["iters"][f]
         np.testing.assert_array_equal(one["x_hat"][0], full["x_hat"][f])
         np.testing.assert_array_equal(one["post"][0], full["post"][f])
