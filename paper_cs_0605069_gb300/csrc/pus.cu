@@ -91,11 +91,12 @@ bool pus_regs_eligible(const DecodeArgs& A) {
     return A.method == kDirect && A.c.q <= 16;
 }
 
-// AUTO takes the thread layout for q >= 8, where a thread's vectors move by
-// 256-bit accesses (GF(16), N = 1000, 20 iterations: 4096 frames 22.5 ms
-// against 25.1 ms for the lane kernel, 760 frames 4.7 against 6.1).
+// AUTO takes the thread layout wherever it applies (q <= 16, probability
+// route), 20 iterations: GF(16), N = 1000, 4096 frames 22.5 ms against 25.1 ms
+// for the lane kernel; GF(8), N = 2000 with a Markov prior, 2048 frames 13.7
+// against 16.8; GF(4), N = 96, 8192 frames 0.93 against 2.66.
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
-    const bool thread = A.layout == GFBP_LAYOUT_THREAD || (A.layout == GFBP_LAYOUT_AUTO && A.c.q >= 8);
+    const bool thread = A.layout != GFBP_LAYOUT_LANES;
     if (thread && pus_regs_eligible(A)) {
         switch (A.c.q) {
         case 2: return launch_regs_q<2>(A, num_sms, s);
