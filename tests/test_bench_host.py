@@ -1,0 +1,58 @@
+"""Host logic of bench.py that needs no GPU: the clock summary taken during
+the timed region, the gating of profiled DRAM traffic on the kernel's source
+files, and the committed profile entries of the benchmark's kernels."""
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    import bench as B
+    return B
+
+
+def test_clock_summary(bench):
+    lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = bench.summarise_clocks(lines)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = bench.summarise_clocks(["0, 1500, 2070, 1400, 0x8, Not Active, Active, Not Active, Not Active"])
+    assert hot["reasons"] == ["hw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
+    assert bench.summarise_clocks([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_profiled_traffic_is_gated_on_the_kernels_sources(bench, tmp_path, monkeypatch):
+    src = tmp_path / "k.cuh"
+    src.write_text("kernel v1\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    entry = {"files": ["k.cuh"], "source_hash": bench.files_hash(["k.cuh"]), "dram_bytes_per_symiter": 500.0}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"k<16>": entry}))
+    assert bench.profiled_traffic("k<16>", 2.0e6) == pytest.approx(1.0e9)
+    assert bench.profiled_traffic("other<16>", 2.0e6) is None
+    src.write_text("kernel v2\n")        # the kernel changed since the counters were taken
+    assert bench.profiled_traffic("k<16>", 2.0e6) is None
+
+
+def test_committed_profiles_cover_the_benchmark_kernels(bench):
+    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for name in bench.BENCH_KERNEL.values():
+        assert name in t, name
+    for name, ent in t.items():
+        assert re.fullmatch(r"[0-9a-f]{16}", ent["source_hash"]), name
+        assert ent["dram_bytes_per_symiter"] > 0
+        for f in ent["files"]:
+            assert os.path.exists(os.path.join(ROOT, f)), f
+        assert os.path.exists(os.path.join(ROOT, ent["capture"])), ent["capture"]
+        text = open(os.path.join(ROOT, ent["capture"])).read()
+        assert "ncu" in text and "--clock-control none" in text
