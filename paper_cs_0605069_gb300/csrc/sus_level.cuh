@@ -22,7 +22,15 @@
 //           stored relabelled into the edge slab.
 // The arithmetic (each sum's order, each product's order, the normalisation)
 // is the single-team kernel's operation for operation, so the two give the
-// same bits.
+// same bits.  A piece's pairs are taken in the regrouped order of
+// CodeDev::lpair_d, each writing the row of its place in the column order.
+//
+// RUN (running partial convolutions, kept in a second global slab): at the
+// start of each sweep every check's suffix convolutions of the sweep-start
+// messages are formed (level_suffixes); step 1 then takes r from the check's
+// running prefix and one suffix (level_check_run) and step 2 extends the
+// prefix by the new message.  sus_level_sm.cuh holds the same arithmetic
+// with the partials in shared memory.
 #pragma once
 
 #include "sus_team.cuh"
