@@ -134,3 +134,23 @@ def test_schedule_validates_like_code_create(G):
     dup = SimpleNamespace(q=4, M=1, N=2, rows=[0, 0], cols=[1, 1], vals=[1, 2])
     with pytest.raises(G.GfbpError):
         G.level_schedule(dup)
+
+
+def test_schedule_edge_cases(G):
+    from types import SimpleNamespace
+    # no checks at all: every column is free, level 0, one pseudo-pair each
+    free = SimpleNamespace(q=4, M=0, N=5, rows=[], cols=[], vals=[])
+    s = G.level_schedule(free)
+    assert list(s["level"]) == [0] * 5 and s["n_levels"] == 1
+    assert sorted(zip(s["pair_col"], s["pair_slot"])) == [(j, 0) for j in range(5)]
+    _check(free, s)
+    # a single column with one check of degree 1
+    one = SimpleNamespace(q=2, M=1, N=1, rows=[0], cols=[0], vals=[1])
+    s = G.level_schedule(one)
+    assert list(s["level"]) == [0] and list(s["piece_ptr"]) == [0, 1]
+    _check(one, s)
+    # one check over 16 columns: a chain of 16 levels of one column each
+    chain = SimpleNamespace(q=4, M=1, N=16, rows=[0] * 16, cols=list(range(16)), vals=[1, 2, 3, 1] * 4)
+    s = G.level_schedule(chain)
+    assert list(s["level"]) == list(range(16)) and len(s["piece_ptr"]) == 17
+    _check(chain, s)
