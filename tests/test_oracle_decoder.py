@@ -254,3 +254,98 @@ def test_step_reproduces_decode(oracle, schedule, markov):
             prior = st["prior_out"]
         if done.all():
             break
+
+
+def _support_propagation(code, C, z, schedule, iters):
+    """BP on the BEC as set propagation: every message is uniform over its
+    support, a coset of GF(2)^p.  Check node: the support of x_j given the
+    others is h_j^-1 (z XOR the sumset of h_j' supp(q_j')); variable node:
+    the intersection of the channel's consistent set with the other checks'
+    supports.  Returns the posterior supports after each iteration."""
+    q = code.q
+    p = q.bit_length() - 1
+    M, N = code.M, code.N
+    rows, cols, vals = (np.asarray(a) for a in (code.rows, code.cols, code.vals))
+    E = len(rows)
+    mul = [[_gf.mul(a, b, p) for b in range(q)] for a in range(q)]
+    inv = [0] + [next(b for b in range(1, q) if mul[a][b] == 1) for a in range(1, q)]
+    edges_of_row = [[e for e in range(E) if rows[e] == i] for i in range(M)]
+    edges_of_col = [[e for e in range(E) if cols[e] == j] for j in range(N)]
+    Qs = [set(C[cols[e]]) for e in range(E)]     # q_ij <- p_j
+    R = [set(range(q)) for _ in range(E)]
+
+    def check(e):
+        i = rows[e]
+        s = {int(z[i])}
+        for e2 in edges_of_row[i]:
+            if e2 != e:
+                s = {a ^ mul[int(vals[e2])][b] for a in s for b in Qs[e2]}
+        return {mul[inv[int(vals[e])]][a] for a in s}
+
+    def var(j):
+        for e in edges_of_col[j]:
+            s = set(C[j])
+            for e2 in edges_of_col[j]:
+                if e2 != e:
+                    s &= R[e2]
+            Qs[e] = s
+
+    def post(j):
+        s = set(C[j])
+        for e in edges_of_col[j]:
+            s &= R[e]
+        return s
+
+    out = []
+    for _ in range(iters):
+        P = [None] * N
+        if schedule == "pus":
+            R = [check(e) for e in range(E)]
+            for j in range(N):
+                var(j)
+                P[j] = post(j)
+        else:
+            for j in range(N):
+                for e in edges_of_col[j]:
+                    R[e] = check(e)
+                P[j] = post(j)
+                var(j)
+        out.append(P)
+    return out
+
+
+# (q, N, erasure rate, seed): cases where decoding progresses over several
+# iterations and the two schedules' support trajectories differ
+BEC_COSET_CASES = [(4, 48, 0.35, 0), (8, 36, 0.30, 5)]
+
+
+@pytest.mark.parametrize("q,N,eps,seed", BEC_COSET_CASES)
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_bec_bit_erasures_follow_coset_propagation(oracle, q, N, eps, seed, schedule):
+    """On a loopy code under random bit erasures every BP posterior is uniform
+    over the support that set propagation predicts, iteration by iteration,
+    in the schedule's own update order (the two orders' trajectories differ
+    here, so the pin tells them apart)."""
+    from paper_cs_0605069_gb300 import workload as W
+    code = W.regular_code(q, N, cfg=f"bec_cosets_{q}_{N}", encodable=False)
+    rng = np.random.default_rng(1000 * seed + q * N)
+    p = q.bit_length() - 1
+    x = rng.integers(0, q, size=N)
+    z = np.asarray(_gf.syndrome(code.rows, code.cols, code.vals, code.M, x, q), np.int64)
+    bits = ((x[:, None] >> np.arange(p)[None, :]) & 1).astype(np.float32)
+    bits[rng.random(bits.shape) < eps] = 2.0
+    C = [{a for a in range(q) if all(bits[j, k] == 2.0 or ((a >> k) & 1) == bits[j, k] for k in range(p))}
+         for j in range(N)]
+    iters = 6
+    want = _support_propagation(code, C, z, schedule, iters)
+    other = _support_propagation(code, C, z, "sus" if schedule == "pus" else "pus", iters)
+    assert want != other
+    msg = oracle.initial_messages(code, bits[None], "bec", eps)
+    for t in range(iters):
+        r = oracle.step(code, bits[None], "bec", eps, msg, schedule, syn=z[None].astype(np.uint8))
+        for j in range(N):
+            S = want[t][j]
+            assert x[j] in S
+            expect = np.array([1.0 / len(S) if a in S else 0.0 for a in range(q)])
+            np.testing.assert_allclose(r["post"][0, j], expect, rtol=0, atol=1e-12, err_msg=f"t={t} j={j}")
+        msg = r["msg"]
