@@ -146,6 +146,41 @@ def test_free_running_gf8_markov_bec(torch_cuda, oracle, schedule):
     _free_running(oracle, _workload("gf8_n2000_markov_bec", 24), "bec", schedule)
 
 
+def sampled_parity(oracle, b, kind, schedule, gpu, frames):
+    """The parity criterion on chosen frames of a batch the GPU decoded whole:
+    the oracle decodes those frames alone (frames are independent).  gpu:
+    outputs of the whole batch (x_hat, iters, converged, trace)."""
+    from tests.parity_util import Batchlike
+    idx = np.asarray(frames)
+    sub = Batchlike(b.code, b.obs[idx], np.asarray(b.param)[idx], b.max_iter)
+    ora = oracle.decode(sub.code, sub.obs, kind, sub.param, schedule, max_iter=sub.max_iter, trace=True)
+    hz = oracle_horizon(oracle, sub.code, sub.obs, kind, sub.param, schedule, sub.max_iter)
+    g = {k: np.asarray(gpu[k])[idx] for k in ("x_hat", "iters", "converged", "trace")}
+    return classify_frames(g, ora, horizon=hz)
+
+
+# The benchmark's launch: 4096 frames of GF(16), N = 1000 at 1.0/1.5/2.0 dB,
+# max 200 iterations, AUTO kernels (SUS: the 64-thread level kernel that
+# folds per visit; PUS: the thread layout).  Frames spread over the batch and
+# the three noise levels are decoded by the oracle one by one.  The horizon
+# share of a batch is bounded by the smaller free-running tests; on a sample
+# of this size only failures are ruled out, and most frames must match.
+BENCH_SAMPLE = [0, 1, 2, 683, 1024, 1366, 2047, 2048, 2730, 3413, 4093, 4094, 4095]
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_benchmark_configuration_sampled_frames(torch_cuda, oracle, schedule):
+    b = _workload("gf16_n1000_awgn", 4096)
+    from paper_cs_0605069_gb300 import gfbp
+    cd = gfbp.Code.from_coo(b.code)
+    gpu = gpu_decode(cd, b.obs, "awgn", b.param, schedule, b.max_iter, trace=True)
+    kinds = sampled_parity(oracle, b, "awgn", schedule, gpu, BENCH_SAMPLE)
+    n = {k: int((kinds == k).sum()) for k in ("match", "tie", "horizon", "fail")}
+    print(f"{schedule} benchmark configuration, sampled frames: {n}")
+    assert n["fail"] == 0, np.asarray(BENCH_SAMPLE)[kinds == "fail"]
+    assert n["match"] >= len(BENCH_SAMPLE) // 2
+
+
 # ---------------------------------------------------------------- edge cases
 def _tiny_codes():
     from tests.test_oracle_decoder import chain_code, random_tree_code
