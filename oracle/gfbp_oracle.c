@@ -38,6 +38,13 @@
  *      P_{K-1} = sum_a Q_{K-2}^a M_ab, initial P = pi (stationary);
  *      transition rows renormalised.
  *   R8 in SUS, Q_j uses the r_ij computed at column j's step.
+ *   R9 Markov prior inside SUS, Gauss-Seidel (markov = 2; a variant the
+ *      paper leaves open): P_i is re-estimated by Eq. 6 just before the
+ *      sweep reaches source symbol i's column, from the pseudo-posteriors of
+ *      its neighbours as they stand (this sweep's where the sweep has already
+ *      passed them, the previous sweep's otherwise); before a symbol's first
+ *      visit its pseudo-posterior is its initial belief p_j (channel
+ *      likelihood times pi, normalised).  No update between sweeps.
  */
 #include <math.h>
 #include <stdint.h>
@@ -366,6 +373,7 @@ typedef struct {
     int schedule;          /* 0 PUS, 1 SUS */
     int use_wht;           /* 0: direct configuration sum, 1: transform route */
     int markov;            /* 0 iid, 1 Markov block priors */
+    int gs;                /* Markov priors re-estimated inside the SUS sweep (R9) */
     const double* Mt;      /* [q*q] row-normalised transition matrix */
     const double* pi;      /* [q] */
     int K;                 /* number of source positions */
@@ -449,6 +457,12 @@ static void one_iteration(const odec* D, owork* W, const uint8_t* z) {
          * column j from the current q; step 2, q_ij for column j; step 3,
          * next column; step 4, Q (computed with column j, R8). */
         for (int j = 0; j < c->N; j++) {
+            if (D->gs && D->src_index[j] >= 0) {   /* R9: P_i as the sweep reaches i */
+                int q = c->q, i = D->src_index[j], K = D->K;
+                const double* Qm = i > 0 ? W->Q + (size_t)D->src_pos[i - 1] * q : NULL;
+                const double* Qp = i < K - 1 ? W->Q + (size_t)D->src_pos[i + 1] * q : NULL;
+                markov_prior_eq6(D->Mt, D->pi, q, Qm, Qp, W->P + (size_t)i * q);
+            }
             for (int k = c->cp[j]; k < c->cp[j + 1]; k++) {
                 int e = c->ce[k];
                 int i = c->er[e];
@@ -547,6 +561,7 @@ static int oshared_init(oshared* S, const oargs* A) {
     S->Mt = malloc(sizeof(double) * (size_t)q * q);
     if (!S->src_index || !S->src_pos || !S->Mt) { oshared_free(S); return OR_ENOMEM; }
     for (int j = 0; j < A->N; j++) S->src_index[j] = -1;
+    if (A->markov == 2 && A->schedule != 1) { oshared_free(S); return OR_EINVAL; }   /* R9: SUS only */
     if (A->markov) {
         if (!A->T || A->K < 1 || A->K > A->N) { oshared_free(S); return OR_EINVAL; }
         for (int a = 0; a < q; a++) { /* R7: rows renormalised */
@@ -568,7 +583,8 @@ static int oshared_init(oshared* S, const oargs* A) {
 
 static void odec_of(odec* D, const oshared* S, const oargs* A, int f) {
     D->g = &S->g; D->c = &S->c; D->kind = A->kind; D->param = A->param ? A->param[f] : 0.0;
-    D->schedule = A->schedule; D->use_wht = A->use_wht; D->markov = A->markov;
+    D->schedule = A->schedule; D->use_wht = A->use_wht; D->markov = A->markov != 0;
+    D->gs = A->markov == 2;
     D->Mt = S->Mt; D->pi = S->pi; D->K = A->markov ? A->K : 0;
     D->src_pos = S->src_pos; D->src_index = S->src_index;
 }
@@ -631,6 +647,9 @@ int oracle_decode(int q, unsigned poly, int M, int N, long E, const int32_t* row
                 for (int k = S.c.cp[j]; k < S.c.cp[j + 1]; k++)
                     memcpy(W.qm + (size_t)S.c.ce[k] * q, W.pj, sizeof(double) * q);
             }
+            /* R9: pseudo-posteriors before any visit are the initial beliefs */
+            if (D.gs)
+                for (int j = 0; j < N; j++) prior_of(&D, &W, j, W.Q + (size_t)j * q);
             int t, ok = 0;
             for (t = 1; t <= max_iter; t++) {
                 one_iteration(&D, &W, z);
@@ -651,7 +670,7 @@ int oracle_decode(int q, unsigned poly, int M, int N, long E, const int32_t* row
                     }
                 }
                 if (ok && early_stop) break;
-                if (t < max_iter && D.markov) {
+                if (t < max_iter && D.markov && !D.gs) {
                     update_priors(&D, &W, W.P);
                 }
             }

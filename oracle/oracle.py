@@ -122,8 +122,10 @@ def _params(param, F):
 
 def decode(code, obs, kind: str, param, schedule: str = "pus", max_iter: int = 100, T=None, K: int = 0,
            src_pos=None, punct=None, syn=None, use_wht: bool | None = None, early_stop: bool = True,
-           trace: bool = False, post: bool = False, threads: int = 0):
-    """Decode F frames.  obs: [F][N][p] (or [F][N][q] for loglik)."""
+           trace: bool = False, post: bool = False, threads: int = 0, gauss_seidel: bool = False):
+    """Decode F frames.  obs: [F][N][p] (or [F][N][q] for loglik).  With a
+    Markov source (T), gauss_seidel re-estimates each block prior as the SUS
+    sweep reaches its symbol instead of after every iteration."""
     obs = _c(obs, np.float32)
     F = obs.shape[0]
     q, M, N = code.q, code.M, code.N
@@ -143,7 +145,7 @@ def decode(code, obs, kind: str, param, schedule: str = "pus", max_iter: int = 1
     rc = lib().oracle_decode(q, int(getattr(code, "poly", 0) or 0), M, N, rows.size, _p(rows), _p(cols), _p(vals),
                              F, KIND[kind], _p(_params(param, F)), _p(obs), _p(_c(punct, np.uint8)),
                              _p(_c(syn, np.uint8)), 1 if schedule == "sus" else 0, int(use_wht), int(early_stop),
-                             int(max_iter), int(markov_on), _p(Tc), int(K if markov_on else 0), _p(sp),
+                             int(max_iter), (2 if gauss_seidel else 1) if markov_on else 0, _p(Tc), int(K if markov_on else 0), _p(sp),
                              _p(xhat), _p(iters), _p(conv), _p(Q), _p(tx), _p(tg), _p(zs), int(threads))
     _check(rc, "oracle_decode")
     out = dict(xhat=xhat, iters=iters, conv=conv, zero_sums=zs)
