@@ -32,19 +32,23 @@ WORKLOAD = "gf16_n1000_awgn"
 # writes every edge message twice per iteration plus the prior (52 q bytes); SUS
 # reads and writes the single stored slab once per sweep plus the prior (28 q).
 ALG_BYTES_PER_SYMITER = {"pus": 52, "sus": 28}
-# Algorithmic FP32 FMAs per symbol-iteration of the probability-domain check
-# node (q <= 16; d_v = 3, d_c = 6, M/N = 1/2), convolutions of q^2 FMAs: PUS
-# runs 3 (d_c - 2) = 12 per check, M/N checks per symbol: 6 q^2.  SUS with
-# running partials: d_c - 2 suffixes per check at the sweep start plus, at each
-# of the d_c - 2 inner positions, one for r and one for the prefix: also
-# 3 (d_c - 2) per check, 6 q^2.  SUS folding per visit: d_c - 2 for each of a
-# column's 3 checks, 12 q^2.
+# FP32 FMAs per symbol-iteration of the probability-domain check node (the
+# route whose every entry keeps relative precision; d_v = 3, d_c = 6, M/N =
+# 1/2), convolutions of q^2 FMAs: PUS runs 3 (d_c - 2) = 12 per check, M/N
+# checks per symbol: 6 q^2.  SUS with running partials: d_c - 2 suffixes per
+# check at the sweep start plus, at each of the d_c - 2 inner positions, one
+# for r and one for the prefix: also 3 (d_c - 2) per check, 6 q^2.  SUS
+# folding per visit: d_c - 2 for each of a column's 3 checks, 12 q^2.
 ALG_FMA_PER_SYMITER_Q2 = {"pus": 6, "sus": 6, "sus_fold": 12}
 # FP32 FMA rate: 152 SMs x 4 schedulers x 32 lanes, one FMA (2 flop) per lane
 # per clock, at the sampled SM clock (2070 MHz maximum).
 FP32_LANES = 152 * 4 * 32
-# The kernel of each schedule on the benchmark path (layout AUTO).
-BENCH_KERNEL = {"pus": "k_pus_regs<16,128>", "sus": "k_sus_level<16,8,64,false>"}
+# The kernel of each schedule on the benchmark path (layout AUTO at 4096
+# frames): PUS frame-resident (a frame's messages in one CTA's shared memory),
+# SUS by levels folding each check's messages per visit (with 27 frames per
+# SM; up to 4 frames per SM AUTO takes the frame-resident SUS kernel).
+BENCH_KERNEL = {"pus": "k_pus_res<16,256,6,4>", "sus": "k_sus_level<16,8,64,false>"}
+RESIDENT_SUS_FRAMES_PER_SM = 4
 
 
 def parse():
@@ -60,7 +64,7 @@ def parse():
     ap.add_argument("--method", default="auto", choices=["auto", "direct", "transform"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sus-width", type=int, default=0, help="SUS lane teams per frame (0 = automatic)")
-    ap.add_argument("--layout", default="auto", choices=["auto", "lanes", "thread"])
+    ap.add_argument("--layout", default="auto", choices=["auto", "lanes", "thread", "resident", "l2resident"])
     ap.add_argument("--partials", default="auto", choices=["auto", "fold", "running", "running_global"],
                     help="SUS level kernel: check messages folded per visit or carried as running partials")
     ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve", "wht", "paper", "fig1"],
@@ -175,10 +179,37 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def code_tokens(text: str) -> str:
+    """C/C++/CUDA source without comments and with whitespace runs collapsed:
+    what the compiler sees, so that an edit of comments alone keeps it."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def files_hash(files) -> str:
+    """Hash of the code (comments and layout aside) of the given source files."""
     h = hashlib.sha256()
     for f in files:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(code_tokens(open(os.path.join(ROOT, f), encoding="utf-8").read()).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
 
 
@@ -194,6 +225,31 @@ def profiled_traffic(kernel: str, symiters: float):
     except (OSError, ValueError, KeyError):
         return None
     return ent["dram_bytes_per_symiter"] * symiters
+
+
+def error_rates(x_hat, x, q: int, levels=(1.0, 1.5, 2.0)):
+    """Frame, symbol and bit error rates of the decided words against the sent
+    codewords, per noise level (frame f is at level f mod len(levels)) and
+    over the batch."""
+    p = q.bit_length() - 1
+    x_hat = np.asarray(x_hat, np.int64)
+    x = np.asarray(x, np.int64)
+    sym = x_hat != x
+    bits = np.zeros(x.shape, np.int64)
+    d = x_hat ^ x
+    for k in range(p):
+        bits += (d >> k) & 1
+
+    def rates(sel):
+        if not sel.any():
+            return None
+        return {"fer": float(sym[sel].any(1).mean()), "ser": float(sym[sel].mean()),
+                "ber": float(bits[sel].sum() / (sel.sum() * x.shape[1] * p)), "frames": int(sel.sum())}
+
+    idx = np.arange(x.shape[0])
+    out = {str(db): rates(idx % len(levels) == k) for k, db in enumerate(levels)}
+    out["all"] = rates(idx >= 0)
+    return out
 
 
 def cpu_baseline(batch, frames: int, max_iter: int):
@@ -244,6 +300,27 @@ def run_reference(args, rank, world):
             "e2e": {"value": val, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "sym_iter_per_s": float(np.mean(its)) * b.code.N / dt}
     print(json.dumps(line), flush=True)
+
+
+def sus_folds(args, frames: int, sms: int = 152) -> bool:
+    """Whether SUS runs the level kernel that folds each check's messages per
+    visit (AUTO above RESIDENT_SUS_FRAMES_PER_SM frames per SM, or asked for)."""
+    if args.partials == "fold":
+        return True
+    if args.layout in ("resident", "l2resident") or args.partials != "auto":
+        return False
+    return args.layout != "auto" or frames > RESIDENT_SUS_FRAMES_PER_SM * sms
+
+
+def launches_per_decode(schedule: str, args, frames: int) -> int:
+    """Kernels one gfbp_decode of the benchmark launches: the channel
+    likelihoods and the schedule's kernel, plus the message initialisation
+    for SUS unless a frame-resident kernel (which initialises on chip) runs."""
+    if schedule == "pus":
+        return 2
+    resident = (args.layout in ("resident", "l2resident") or
+                (args.layout == "auto" and args.partials == "auto" and not sus_folds(args, frames)))
+    return 2 if resident else 3
 
 
 def main():
@@ -374,11 +451,14 @@ def main():
         it = np.stack(iters[s])
         symit = float(it.sum()) * N / args.steps
         kms = float(np.mean(kern_ms[s]))
+        conv = outs[s]["converged"].cpu().numpy().astype(bool)
+        last = it[-1]
         per[s] = {"kernel_ms": kms, "frames_per_s": F / (kms / 1e3), "sym_iter_per_s": symit / (kms / 1e3),
-                  "mean_iters": float(it.mean()), "mean_iters_converged": None,
+                  "mean_iters": float(it.mean()),
+                  "mean_iters_converged": float(last[conv].mean()) if conv.any() else None,
                   "iters_by_ebn0_db": {str(db): float(it[:, k::3].mean()) for k, db in enumerate((1.0, 1.5, 2.0))},
-                  "converged": float(outs[s]["converged"].float().mean().item())}
-        per[s]["mean_iters_converged"] = None
+                  "converged": float(conv.mean()),
+                  "errors_by_ebn0_db": error_rates(outs[s]["x_hat"].cpu().numpy(), b.x, q)}
     # roofline of the dominant kernel: the FP32 FMA pipe (the probability-domain
     # check node's q^2 convolutions) and the HBM model of the paper's passes;
     # "bound" is the nearer of the two ceilings
@@ -390,11 +470,10 @@ def main():
     hbm_gbs = ALG_BYTES_PER_SYMITER[dom] * q * symit_launch / secs / 1e9
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     alu_peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-    # AUTO folds per visit at the benchmark's 27 frames per SM
-    fma_key = "sus_fold" if dom == "sus" and args.partials in ("auto", "fold") else dom
+    fma_key = "sus_fold" if dom == "sus" and sus_folds(args, F) else dom
     alu_tf = 2 * ALG_FMA_PER_SYMITER_Q2[fma_key] * q * q * symit_launch / secs / 1e12
     kernel = (BENCH_KERNEL[dom] if args.layout == "auto" and args.method == "auto" and args.partials == "auto"
-              else None)
+              and not (dom == "sus" and not sus_folds(args, F)) else None)
     traffic = profiled_traffic(kernel, symit_launch) if kernel else None
     hbm = {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
            "peak_source": "measured" if peaks else "fallback",
@@ -402,10 +481,11 @@ def main():
     alu = {"achieved": alu_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_tf / alu_peak,
            "peak_source": f"derived: {FP32_LANES} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sampled SM clock)",
            "algorithmic_flops_per_symiter": 2 * ALG_FMA_PER_SYMITER_Q2[fma_key] * q * q}
-    main, other, bound = (alu, hbm, "alu") if alu["frac"] >= hbm["frac"] else (hbm, alu, "hbm")
-    roof = {"bound": bound, **main, "traffic": traffic, "kernel": kernel or f"{dom} ({args.layout}/{args.method})",
-            ("hbm_model" if bound == "alu" else "alu_model"): other}
-    gpu_launches = args.steps * sum(2 if s == "pus" else 3 for s in scheds)  # channel (+ SUS init) + decode
+    # headline: the HBM roofline of the method's algorithmic bytes per
+    # symbol-iteration; the FP32 FMA figure of the same launch beside it
+    roof = {"bound": "hbm", **hbm, "traffic": traffic, "kernel": kernel or f"{dom} ({args.layout}/{args.method})",
+            "alu_model": alu}
+    gpu_launches = args.steps * sum(launches_per_decode(s, args, F) for s in scheds)
 
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

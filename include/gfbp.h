@@ -114,13 +114,23 @@ typedef struct {
 
 typedef enum { GFBP_PUS = 0, GFBP_SUS = 1 } gfbp_schedule;
 
-typedef enum { GFBP_PRIOR_IID = 0, GFBP_PRIOR_MARKOV = 1 } gfbp_prior_kind;
+typedef enum { GFBP_PRIOR_IID = 0, GFBP_PRIOR_MARKOV = 1, GFBP_PRIOR_MARKOV_GS = 2 } gfbp_prior_kind;
 
 /*
  * Source prior (Sec. 2).  I.i.d.: Pr(s = a) = 1/q for every symbol.  Markov:
  * dynamical block priors re-estimated after every iteration by Eq. 6-7 from
  * the pseudo-posteriors of the neighbouring source symbols; every other symbol
  * keeps the uniform prior.
+ * MARKOV_GS (a variant the paper leaves open; SUS with gfbp_decode only): the
+ * block prior of source symbol i is re-estimated by Eq. 6 just before the
+ * sweep reaches its column, from its neighbours' pseudo-posteriors as they
+ * stand at that moment (this sweep's where the sweep has passed them, the
+ * previous sweep's otherwise; before a symbol's first visit, its initial
+ * belief: channel likelihood times the stationary distribution, normalised),
+ * and not between sweeps.  The sweep is then a chain through the source
+ * symbols, so it runs on the column-walking kernel (a lane group per frame;
+ * q <= 16, or the TRANSFORM check method for q >= 32).  PUS, gfbp_step,
+ * batches and the server return GFBP_EUNSUPPORTED for it.
  */
 typedef struct {
     int32_t kind;           /* gfbp_prior_kind */
@@ -140,14 +150,20 @@ typedef struct {
  *              1e-7 of the largest.
  *   DIRECT     the configuration sum by successive XOR-convolutions of the
  *              relabelled messages, non-negative arithmetic only, every entry
- *              to relative precision (q <= 16).
+ *              to relative precision (any q; q^2 FMAs per convolution, in
+ *              registers for q <= 16, from shared memory by lane groups for
+ *              q >= 32).
  *   TENSOR     the convolution theorem with plain transforms stored (F =
  *              WHT of the relabelled q), the transforms inside the sweep taken
  *              as dense +-1 Hadamard contractions on the tensor cores (FP16
  *              hi/lo split of power-of-two-scaled vectors, FP32 accumulation;
  *              gfbp_wht).  SUS only, q >= 16; posteriors within 1e-4 of the
  *              FP64 oracle per iteration (tested).
- *   AUTO       DIRECT for q <= 16, TRANSFORM above.
+ *   AUTO       DIRECT for q <= 64 (posteriors within 1e-5 of the FP64 oracle
+ *              per iteration, tested), TRANSFORM for q = 128, 256, where
+ *              DIRECT's q^2 FMAs per convolution (65536 at q = 256) make long
+ *              decodes impractical; DIRECT stays available there (within 1e-5,
+ *              tested).  TENSOR is an explicit choice.
  */
 typedef enum {
     GFBP_CHECK_AUTO = 0,
@@ -170,13 +186,38 @@ typedef enum {
  *           the highest level of the earlier columns sharing a check with j;
  *           one level's columns share no check) and a level's (column, check)
  *           pairs run at once, a thread each.
- *   AUTO    THREAD (PUS, measured against LANES: 10% faster on GF(16),
- *           N = 1000; 18% on GF(8), N = 2000; 2.9x on GF(4), N = 96).
+ *   RESIDENT  THREAD's arithmetic with the frame's whole edge slab held in
+ *           one CTA's shared memory from the first iteration to the last
+ *           (E q 4 bytes plus about 10 KB must fit the opt-in shared memory
+ *           of a CTA, 227 KB on GB300: GF(16) up to about 3,500 edges).  The
+ *           messages never travel to global memory; a sweep reads only the
+ *           frame's channel likelihoods and block priors.  PUS: the bits of
+ *           THREAD (row degree <= 6, column degree <= 4).  SUS: the bits of
+ *           THREAD with RUNNING partials (the partial convolutions replace
+ *           the check's messages in their own slots), so sus_partials must be
+ *           AUTO or RUNNING.  GFBP_EUNSUPPORTED where it does not apply.
+ *   L2RESIDENT  (SUS) RESIDENT's kernel and bits with each CTA's slab in
+ *           the workspace instead of shared memory, and only as many CTAs at
+ *           once as keep all their slabs within 75% of the L2 (several per
+ *           SM for GF(16), N = 1000), so that the messages stay on chip and
+ *           the CTAs' latencies overlap; any code size (q <= 16).
+ *   AUTO    PUS: RESIDENT where it applies, else THREAD; SUS: RESIDENT up
+ *           to 4 frames per SM (AUTO partials; where one frame's latency
+ *           sets the time), else THREAD, whose many frames per SM hide each
+ *           other's latency (PUS THREAD measured against
+ *           LANES: 10% faster on GF(16), N = 1000; 18% on GF(8), N = 2000;
+ *           2.9x on GF(4), N = 96).
  * SUS with the TRANSFORM check node (any q) also runs by levels unless LANES
  * is asked for: a lane group per (column, check) pair instead of per frame,
  * the same bits as the lane kernel.
  */
-typedef enum { GFBP_LAYOUT_AUTO = 0, GFBP_LAYOUT_LANES = 1, GFBP_LAYOUT_THREAD = 2 } gfbp_layout;
+typedef enum {
+    GFBP_LAYOUT_AUTO = 0,
+    GFBP_LAYOUT_LANES = 1,
+    GFBP_LAYOUT_THREAD = 2,
+    GFBP_LAYOUT_RESIDENT = 3,
+    GFBP_LAYOUT_L2RESIDENT = 4
+} gfbp_layout;
 
 /*
  * How the SUS level kernel (THREAD layout, DIRECT check node, q <= 16)
@@ -200,14 +241,14 @@ typedef enum { GFBP_LAYOUT_AUTO = 0, GFBP_LAYOUT_LANES = 1, GFBP_LAYOUT_THREAD =
  *            (a second edge slab, F E q 4 bytes, allocated stream-ordered by
  *            the call itself; refused by gfbp_decode_noalloc): the same bits
  *            as RUNNING.
- *   AUTO     RUNNING for at most one frame per SM, where one frame's
- *            latency sets the decode time (GF(16), N = 1000: 1.34x faster
- *            than FOLD at one frame per SM), FOLD above (with several frames
- *            resident per SM it is faster: 28 ms against 48 ms for 4096
- *            frames x 20 iterations).  The choice follows the frame count, so
- *            a frame's posteriors can differ in the last bits between a call
- *            with few frames and one with many; FOLD or RUNNING fix the
- *            kernel and with it the bits.
+ *   AUTO     RUNNING up to 4 frames per SM (with layout AUTO the frame's
+ *            partials in shared memory, the RESIDENT kernel: GF(16), N =
+ *            1000, 20 iterations, 152 frames 1.49 ms against 2.41 ms for
+ *            FOLD), FOLD above (with many frames resident per SM their
+ *            latencies overlap: 4096 frames 19.6 ms against 24.5 ms).  The
+ *            choice follows the frame count, so a frame's posteriors can
+ *            differ in the last bits between a call with few frames and one
+ *            with many; FOLD or RUNNING fix the kernel and with it the bits.
  * Other kernels ignore the option.
  */
 typedef enum {
@@ -377,10 +418,13 @@ void gfbp_batch_destroy(gfbp_batch* batch);
  * Synchronous; allocates its own scratch.  *chosen receives the variant:
  * 0-2 team q = 4/8/16, 3-6 group probability route q = 2/4/8/16,
  * 7-10 group transform route q = 32/64/128/256, 11-14 levels probability
- * route q = 2/4/8/16, 15-18 levels transform route q = 32/64/128/256 (the
- * default without tuning: 11-18).  PUS has one variant per q.  Variants 19-23
- * (levels, TENSOR check method, q = 16/32/64/128/256) are never chosen here;
- * gfbp_batch_set_variants takes them.
+ * route q = 2/4/8/16, 15-18 levels transform route q = 32/64/128/256,
+ * 19-23 levels TENSOR route q = 16/32/64/128/256, 24-27 levels probability
+ * route by lane groups q = 32/64/128/256.  Items decode by AUTO's route (the
+ * default without tuning: 11-14, 24-25 and 17-18), so this chooses among its
+ * variants only; PUS has one variant per q.  The variants of the other
+ * routes (7-8 and 15-16, 26-27, 19-23) are explicit choices for
+ * gfbp_batch_set_variants.
  */
 gfbp_status gfbp_autotune(const gfbp_code* code, int32_t n_frames, const float* obs, gfbp_channel channel,
                           gfbp_schedule schedule, const gfbp_prior* prior, int32_t max_iter, void* stream,

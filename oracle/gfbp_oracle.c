@@ -374,6 +374,7 @@ typedef struct {
     int use_wht;           /* 0: direct configuration sum, 1: transform route */
     int markov;            /* 0 iid, 1 Markov block priors */
     int gs;                /* Markov priors re-estimated inside the SUS sweep (R9) */
+    int round32;           /* conditioning probe: store every message rounded to float */
     const double* Mt;      /* [q*q] row-normalised transition matrix */
     const double* pi;      /* [q] */
     int K;                 /* number of source positions */
@@ -396,6 +397,16 @@ typedef struct {
     long zero_sums;
 } owork;
 
+/* The conditioning probe (not the decoder's arithmetic; round32 != 0): a
+ * message stored rounded to the nearest float, as a decoder that keeps FP32
+ * messages does.  With round32 = k >= 2 every channel likelihood is also moved
+ * by one float ulp up, down or not at all, by a hash of (k, frame, symbol,
+ * entry): one of the FP32 roundings a decoder computing them could meet. */
+static void store32(const odec* D, double* v, int q) {
+    if (D->round32)
+        for (int a = 0; a < q; a++) v[a] = (double)(float)v[a];
+}
+
 /* p_j = L_j * P_j, normalised (Sec. 2 priors; i.i.d. source: uniform, no effect). */
 static void prior_of(const odec* D, const owork* W, int j, double* out) {
     int q = D->g->q;
@@ -417,6 +428,7 @@ static void horizontal_check(const odec* D, owork* W, int i, int z_i, int only_e
         if (D->use_wht) check_edge_wht(D->g, d, W->h, (const double* const*)W->qv, k, z_i, r, W->u, W->v);
         else check_edge_direct(D->g, d, W->h, (const double* const*)W->qv, k, z_i, r, W->u, W->v);
         W->zero_sums += normalise(r, q);
+        store32(D, r, q);
     }
 }
 
@@ -434,6 +446,7 @@ static void vertical_column(const odec* D, owork* W, int j) {
             qo[a] = v;
         }
         W->zero_sums += normalise(qo, q);
+        store32(D, qo, q);
     }
     double* Qj = W->Q + (size_t)j * q;
     for (int a = 0; a < q; a++) {
@@ -442,6 +455,7 @@ static void vertical_column(const odec* D, owork* W, int j) {
         Qj[a] = v;
     }
     W->zero_sums += normalise(Qj, q);
+    store32(D, Qj, q);
 }
 
 /* One iteration of the chosen schedule, ending with Q for every symbol. */
@@ -532,6 +546,7 @@ typedef struct {
     int schedule, use_wht, early_stop, max_iter;
     int markov; const double* T; int K; const int32_t* src_pos;
     int n_threads;
+    int round32;              /* conditioning probe (store32) */
 } oargs;
 
 typedef struct {
@@ -585,17 +600,36 @@ static void odec_of(odec* D, const oshared* S, const oargs* A, int f) {
     D->g = &S->g; D->c = &S->c; D->kind = A->kind; D->param = A->param ? A->param[f] : 0.0;
     D->schedule = A->schedule; D->use_wht = A->use_wht; D->markov = A->markov != 0;
     D->gs = A->markov == 2;
+    D->round32 = A->round32;
     D->Mt = S->Mt; D->pi = S->pi; D->K = A->markov ? A->K : 0;
     D->src_pos = S->src_pos; D->src_index = S->src_index;
 }
 
 /* Channel likelihoods of frame f and the initial priors (pi for source symbols). */
+static uint64_t mix64(uint64_t x) {   /* splitmix64 finaliser */
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
 static void frame_setup(const odec* D, owork* W, const oargs* A, int f) {
     int q = A->q, p = D->g->p, N = A->N;
     int stride = A->kind == CH_LOGLIK ? q : p;
-    for (int j = 0; j < N; j++)
+    for (int j = 0; j < N; j++) {
+        double* L = W->L + (size_t)j * q;
         channel_likelihood(A->kind, D->param, q, p, A->obs + ((size_t)f * N + j) * stride,
-                           A->punct ? A->punct[j] : 0, W->L + (size_t)j * q);
+                           A->punct ? A->punct[j] : 0, L);
+        if (D->round32 >= 2)
+            for (int a = 0; a < q; a++) {
+                const uint64_t h = mix64(((uint64_t)D->round32 << 48) ^ ((uint64_t)f << 32) ^ ((uint64_t)j << 9) ^ a);
+                const float x = (float)L[a];
+                const int step = (int)(h % 3) - 1;
+                L[a] = step == 0 || x == 0.0f ? x : nextafterf(x, step > 0 ? INFINITY : 0.0f);
+            }
+        else
+            store32(D, L, q);
+    }
     for (int i = 0; i < D->K; i++)
         for (int a = 0; a < q; a++) W->P[(size_t)i * q + a] = D->pi[a];
 }
@@ -611,9 +645,9 @@ int oracle_decode(int q, unsigned poly, int M, int N, long E, const int32_t* row
                   const uint8_t* punct, const uint8_t* syn, int schedule, int use_wht, int early_stop,
                   int max_iter, int markov, const double* T, int K, const int32_t* src_pos, uint8_t* xhat,
                   int32_t* iters, uint8_t* conv, double* post, uint8_t* trace_x, float* trace_gap,
-                  int64_t* zero_sums, int n_threads) {
+                  int64_t* zero_sums, int n_threads, int round32) {
     oargs A = {q, poly, M, N, E, row, col, val, n_frames, kind, param, obs, punct, syn,
-               schedule, use_wht, early_stop, max_iter, markov, T, K, src_pos, n_threads};
+               schedule, use_wht, early_stop, max_iter, markov, T, K, src_pos, n_threads, round32};
     oshared S;
     int rc = oshared_init(&S, &A);
     if (rc) return rc;
@@ -703,7 +737,7 @@ int oracle_step(int q, unsigned poly, int M, int N, long E, const int32_t* row, 
                 const double* T, int K, const int32_t* src_pos, double* msg, const double* prior,
                 double* prior_out, double* post, uint8_t* xhat, uint8_t* sat, int n_threads) {
     oargs A = {q, poly, M, N, E, row, col, val, n_frames, kind, param, obs, punct, syn,
-               schedule, use_wht, 1, 1, markov, T, K, src_pos, n_threads};
+               schedule, use_wht, 1, 1, markov, T, K, src_pos, n_threads, 0};
     oshared S;
     int rc = oshared_init(&S, &A);
     if (rc) return rc;

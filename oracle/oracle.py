@@ -44,7 +44,7 @@ def lib():
             P = C.c_void_p
             i, u, l, d = C.c_int, C.c_uint, C.c_long, C.c_double
             _lib.oracle_decode.argtypes = [i, u, i, i, l, P, P, P, i, i, P, P, P, P, i, i, i, i, i, P, i, P,
-                                           P, P, P, P, P, P, P, i]
+                                           P, P, P, P, P, P, P, i, i]
             _lib.oracle_step.argtypes = [i, u, i, i, l, P, P, P, i, i, P, P, P, P, i, i, i, P, i, P,
                                          P, P, P, P, P, P, i]
             _lib.oracle_gf_tables.argtypes = [i, u, P, P]
@@ -122,10 +122,15 @@ def _params(param, F):
 
 def decode(code, obs, kind: str, param, schedule: str = "pus", max_iter: int = 100, T=None, K: int = 0,
            src_pos=None, punct=None, syn=None, use_wht: bool | None = None, early_stop: bool = True,
-           trace: bool = False, post: bool = False, threads: int = 0, gauss_seidel: bool = False):
+           trace: bool = False, post: bool = False, threads: int = 0, gauss_seidel: bool = False,
+           round32: int = 0):
     """Decode F frames.  obs: [F][N][p] (or [F][N][q] for loglik).  With a
     Markov source (T), gauss_seidel re-estimates each block prior as the SUS
-    sweep reaches its symbol instead of after every iteration."""
+    sweep reaches its symbol instead of after every iteration.  round32 is a
+    conditioning probe, not the decoder: with round32 != 0 every message is
+    stored rounded to the nearest float, as a decoder keeping FP32 messages
+    does, and with round32 = k >= 2 the channel likelihoods are also moved by
+    one float ulp in a pattern seeded by k."""
     obs = _c(obs, np.float32)
     F = obs.shape[0]
     q, M, N = code.q, code.M, code.N
@@ -146,7 +151,8 @@ def decode(code, obs, kind: str, param, schedule: str = "pus", max_iter: int = 1
                              F, KIND[kind], _p(_params(param, F)), _p(obs), _p(_c(punct, np.uint8)),
                              _p(_c(syn, np.uint8)), 1 if schedule == "sus" else 0, int(use_wht), int(early_stop),
                              int(max_iter), (2 if gauss_seidel else 1) if markov_on else 0, _p(Tc), int(K if markov_on else 0), _p(sp),
-                             _p(xhat), _p(iters), _p(conv), _p(Q), _p(tx), _p(tg), _p(zs), int(threads))
+                             _p(xhat), _p(iters), _p(conv), _p(Q), _p(tx), _p(tg), _p(zs), int(threads),
+                             int(round32))
     _check(rc, "oracle_decode")
     out = dict(xhat=xhat, iters=iters, conv=conv, zero_sums=zs)
     if post:

@@ -49,12 +49,13 @@ enum Variant : int {
     kLevel2D, kLevel4D, kLevel8D, kLevel16D,                  // SUS levels, probability route (CTA family)
     kLevel32T, kLevel64T, kLevel128T, kLevel256T,             // SUS levels, transform route (CTA family)
     kLevel16X, kLevel32X, kLevel64X, kLevel128X, kLevel256X,  // SUS levels, tensor-core route (CTA family)
+    kLevel32D, kLevel64D, kLevel128D, kLevel256D,             // SUS levels, probability route, lane groups (CTA family)
     kNumVariants
 };
 
 // Check-node route a variant computes (the item's DecodeArgs::method).
 int variant_method(int v) {
-    if (v >= kLevel16X) return kTensor;
+    if (v >= kLevel16X && v <= kLevel256X) return kTensor;
     if ((v >= kGroup32T && v <= kGroup256T) || (v >= kLevel32T && v <= kLevel256T)) return kTransform;
     return kDirect;
 }
@@ -71,6 +72,10 @@ int tensor_variant(int q) {
 }
 
 __host__ __device__ constexpr bool cta_variant(int v) { return v >= kLevel2D; }
+
+// CTA-family variants that work with a lane group per pair (q >= 32 and the
+// tensor-core route): their CTAs take 256 threads.
+__host__ __device__ constexpr bool lane_group_variant(int v) { return cta_variant(v) && !(v >= kLevel2D && v <= kLevel16D); }
 
 // SUS CTA family: one frame per CTA, 256 threads when a transform-route item
 // (a lane group per pair) is in the launch, else 128 (a thread per pair).
@@ -105,12 +110,12 @@ __device__ __noinline__ void sus_level_call(const DecodeArgs& A, int f, const ui
     sus_level_frame<Q, 8, T, false>(A, f, mul, div, dyn, dyn + kLevelPiece * level_rs<Q>());
 }
 
-template <int Q, int T>
+template <int Q, int T, int METHOD>
 __device__ __noinline__ void sus_level_tr_call(const DecodeArgs& A, int f, const uint8_t* ex, const uint8_t* lg,
                                                float* dyn) {
     constexpr int G = Lay<Q>::G;
     float* sc = dyn + (size_t)level_tr_sub<Q>() * Q + (size_t)(threadIdx.x / G) * (Q + 4);
-    sus_level_tr_frame<Q, T>(A, f, ex, lg, dyn, sc);
+    sus_level_tr_frame<Q, T, METHOD>(A, f, ex, lg, dyn, sc);
 }
 
 template <int Q, int T>
@@ -138,6 +143,10 @@ size_t cta_variant_smem(int v) {
     case kLevel64T: return level_mixed_bytes<64, T>();
     case kLevel128T: return level_mixed_bytes<128, T>();
     case kLevel256T: return level_mixed_bytes<256, T>();
+    case kLevel32D: return level_mixed_bytes<32, T>();
+    case kLevel64D: return level_mixed_bytes<64, T>();
+    case kLevel128D: return level_mixed_bytes<128, T>();
+    case kLevel256D: return level_mixed_bytes<256, T>();
     case kLevel16X: return TcLay<16, T>::total;
     case kLevel32X: return TcLay<32, T>::total;
     case kLevel64X: return TcLay<64, T>::total;
@@ -193,7 +202,7 @@ __global__ void __launch_bounds__(kMixedThreads) k_sus_mixed(const DecodeArgs* _
                                                              const int* __restrict__ prefix,
                                                              const int* __restrict__ variant, int n_items,
                                                              int total, int* counter, const int* field_item) {
-    __shared__ FieldTables T;
+    __shared__ __align__(16) FieldTables T;
     __shared__ __align__(16) float s_scr[(kMixedThreads / 32) * kWarpScratch];
     const int tid = threadIdx.x;
     load_fields(T, items, field_item, tid, blockDim.x);
@@ -260,7 +269,7 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_sus_mixed_cta(const DecodeAr
                                                                     const int* __restrict__ prefix,
                                                                     const int* __restrict__ variant, int n_items,
                                                                     int total, int* counter, const int* field_item) {
-    __shared__ FieldTables T;
+    __shared__ __align__(16) FieldTables T;
     __shared__ int s_frame;
     extern __shared__ __align__(16) float s_dyn[];
     const int tid = threadIdx.x;
@@ -286,26 +295,38 @@ __global__ void __launch_bounds__(NTH, 512 / NTH) k_sus_mixed_cta(const DecodeAr
         case kLevel4D: sus_level_call<4, NTH>(A, f, mul, div, s_dyn); break;
         case kLevel8D: sus_level_call<8, NTH>(A, f, mul, div, s_dyn); break;
         case kLevel16D: sus_level_call<16, NTH>(A, f, mul, div, s_dyn); break;
-        case kLevel32T: sus_level_tr_call<32, NTH>(A, f, ex, lg, s_dyn); break;
-        case kLevel64T: sus_level_tr_call<64, NTH>(A, f, ex, lg, s_dyn); break;
-        case kLevel128T: sus_level_tr_call<128, NTH>(A, f, ex, lg, s_dyn); break;
-        case kLevel256T: sus_level_tr_call<256, NTH>(A, f, ex, lg, s_dyn); break;
+        case kLevel32T: sus_level_tr_call<32, NTH, kTransform>(A, f, ex, lg, s_dyn); break;
+        case kLevel64T: sus_level_tr_call<64, NTH, kTransform>(A, f, ex, lg, s_dyn); break;
+        case kLevel128T: sus_level_tr_call<128, NTH, kTransform>(A, f, ex, lg, s_dyn); break;
+        case kLevel256T: sus_level_tr_call<256, NTH, kTransform>(A, f, ex, lg, s_dyn); break;
+        case kLevel32D: sus_level_tr_call<32, NTH, kDirect>(A, f, ex, lg, s_dyn); break;
+        case kLevel64D: sus_level_tr_call<64, NTH, kDirect>(A, f, ex, lg, s_dyn); break;
+        case kLevel128D: sus_level_tr_call<128, NTH, kDirect>(A, f, ex, lg, s_dyn); break;
+        case kLevel256D: sus_level_tr_call<256, NTH, kDirect>(A, f, ex, lg, s_dyn); break;
         case kLevel16X: sus_level_tc_call<16, NTH>(A, f, ex, lg, s_dyn); break;
         case kLevel32X: sus_level_tc_call<32, NTH>(A, f, ex, lg, s_dyn); break;
         case kLevel64X: sus_level_tc_call<64, NTH>(A, f, ex, lg, s_dyn); break;
         case kLevel128X: sus_level_tc_call<128, NTH>(A, f, ex, lg, s_dyn); break;
-        default: sus_level_tc_call<256, NTH>(A, f, ex, lg, s_dyn); break;
+        case kLevel256X: sus_level_tc_call<256, NTH>(A, f, ex, lg, s_dyn); break;
+        default: break;
         }
     }
 }
 
-// PUS: one CTA per frame, the item's q picks the routine.
-constexpr int kMixedPusScratch = 256 * (8 * 4 + 4);  // largest pus_group_scratch over the variants (q = 4)
+// PUS: one CTA per frame, the item's q and check-node route pick the routine.
+template <int Q>
+constexpr int pus_mixed_scratch() { return (kPusThreads / Lay<Q>::G) * pus_group_scratch<Q, 6, kDirect>(); }
+constexpr int imax(int a, int b) { return a > b ? a : b; }
+// the largest over the variants (the probability route needs the most)
+constexpr int kMixedPusScratch =
+    imax(imax(imax(pus_mixed_scratch<2>(), pus_mixed_scratch<4>()), imax(pus_mixed_scratch<8>(), pus_mixed_scratch<16>())),
+         imax(imax(pus_mixed_scratch<32>(), pus_mixed_scratch<64>()),
+              imax(pus_mixed_scratch<128>(), pus_mixed_scratch<256>())));
 
 __global__ void __launch_bounds__(kPusThreads) k_pus_mixed(const DecodeArgs* __restrict__ items,
                                                            const int* __restrict__ prefix, int n_items, int total,
                                                            int* counter, const int* field_item) {
-    __shared__ FieldTables T;
+    __shared__ __align__(16) FieldTables T;
     __shared__ int s_frame;
     extern __shared__ __align__(16) float s_scr[];
     const int tid = threadIdx.x;
@@ -326,10 +347,22 @@ __global__ void __launch_bounds__(kPusThreads) k_pus_mixed(const DecodeArgs* __r
         case 4: pus_call<4, kDirect>(A, f, ex, lg, s_scr); break;
         case 8: pus_call<8, kDirect>(A, f, ex, lg, s_scr); break;
         case 16: pus_call<16, kDirect>(A, f, ex, lg, s_scr); break;
-        case 32: pus_call<32, kTransform>(A, f, ex, lg, s_scr); break;
-        case 64: pus_call<64, kTransform>(A, f, ex, lg, s_scr); break;
-        case 128: pus_call<128, kTransform>(A, f, ex, lg, s_scr); break;
-        default: pus_call<256, kTransform>(A, f, ex, lg, s_scr); break;
+        case 32:
+            if (A.method == kDirect) pus_call<32, kDirect>(A, f, ex, lg, s_scr);
+            else pus_call<32, kTransform>(A, f, ex, lg, s_scr);
+            break;
+        case 64:
+            if (A.method == kDirect) pus_call<64, kDirect>(A, f, ex, lg, s_scr);
+            else pus_call<64, kTransform>(A, f, ex, lg, s_scr);
+            break;
+        case 128:
+            if (A.method == kDirect) pus_call<128, kDirect>(A, f, ex, lg, s_scr);
+            else pus_call<128, kTransform>(A, f, ex, lg, s_scr);
+            break;
+        default:
+            if (A.method == kDirect) pus_call<256, kDirect>(A, f, ex, lg, s_scr);
+            else pus_call<256, kTransform>(A, f, ex, lg, s_scr);
+            break;
         }
     }
 }
@@ -340,11 +373,25 @@ int default_variant(int q) {
     case 4: return kLevel4D;
     case 8: return kLevel8D;
     case 16: return kLevel16D;
-    case 32: return kLevel32T;
-    case 64: return kLevel64T;
+    case 32: return kLevel32D;
+    case 64: return kLevel64D;
     case 128: return kLevel128T;
     default: return kLevel256T;
     }
+}
+
+// The variants of the route AUTO does not take for q >= 32: the transform
+// route for q = 32, 64 (trading the probability route's relative precision
+// for speed), the probability route for q = 128, 256 (exact, at q^2 FMAs per
+// convolution).
+std::vector<int> other_route_variants(int q) {
+    switch (q) {
+    case 32: return {kLevel32T, kGroup32T};
+    case 64: return {kLevel64T, kGroup64T};
+    case 128: return {kLevel128D};
+    case 256: return {kLevel256D};
+    }
+    return {};
 }
 
 // SUS variants the autotuner may pick from (same check-node route, so the
@@ -356,19 +403,14 @@ std::vector<int> sus_candidates(int q) {
     case 4: return {kLevel4D, kTeam4, kGroup4D};
     case 8: return {kLevel8D, kTeam8, kGroup8D};
     case 16: return {kLevel16D, kTeam16, kGroup16D};
-    case 32: return {kLevel32T, kGroup32T};
-    case 64: return {kLevel64T, kGroup64T};
+    case 32: return {kLevel32D};
+    case 64: return {kLevel64D};
     case 128: return {kLevel128T, kGroup128T};
     default: return {kLevel256T, kGroup256T};
     }
 }
 
-int num_sms() {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    return v > 0 ? v : 1;
-}
+int num_sms() { return device_sms(); }
 
 // autotuner cache: (device, q, N, M, E, schedule) -> variant
 std::mutex g_tune_mu;
@@ -423,35 +465,26 @@ void mixed_shape(MixedLaunch& m, const int* variants) {
         m.cta_threads = 128;
         for (int i = 0; i < m.n_items; i++) {
             (cta_variant(variants[i]) ? m.has_cta : m.has_warp) = true;
-            if (cta_variant(variants[i]) && variant_method(variants[i]) != kDirect) m.cta_threads = 256;
+            if (lane_group_variant(variants[i])) m.cta_threads = 256;
         }
         m.cta_smem = 0;
         for (int i = 0; i < m.n_items; i++)
             m.cta_smem = max2(m.cta_smem, m.cta_threads == 256 ? cta_variant_smem<256>(variants[i])
                                                                : cta_variant_smem<128>(variants[i]));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_mixed, kMixedThreads, 0);
+        kernel_prepare((const void*)k_sus_mixed, kMixedThreads, 0, &occ);
         const long long want = ((long long)m.total + 3) / 4;
         const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
         m.grid = (int)(want < cap ? want : cap);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_sus_mixed_cta<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cta_smem_max<128>());
-            cudaFuncSetAttribute(k_sus_mixed_cta<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cta_smem_max<256>());
-            attr = true;
-        }
         int occ2 = 1;
         if (m.cta_threads == 256)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_sus_mixed_cta<256>, 256, m.cta_smem);
+            kernel_prepare((const void*)k_sus_mixed_cta<256>, 256, m.cta_smem, &occ2);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_sus_mixed_cta<128>, 128, m.cta_smem);
+            kernel_prepare((const void*)k_sus_mixed_cta<128>, 128, m.cta_smem, &occ2);
         const long long cap2 = (long long)num_sms() * (occ2 > 0 ? occ2 : 1);
         m.grid_cta = (int)(m.total < cap2 ? m.total : cap2);
     } else {
         m.pus_smem = sizeof(float) * (size_t)kMixedPusScratch;
-        cudaFuncSetAttribute(k_pus_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.pus_smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus_mixed, kPusThreads, m.pus_smem);
+        kernel_prepare((const void*)k_pus_mixed, kPusThreads, m.pus_smem, &occ);
         const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
         m.grid = (int)(m.total < cap ? m.total : cap);
     }
@@ -594,7 +627,7 @@ extern "C" gfbp_status gfbp_batch_create(const gfbp_batch_item* items, int32_t n
     for (int i = 0; i < n_items; i++) {
         const gfbp_batch_item& it = items[i];
         const int q = it.code->dev.q;
-        const int method = q <= 16 ? kDirect : kTransform;
+        const int method = q <= kAutoDirectMaxQ ? kDirect : kTransform;
         e = batch_prepare_item(b->args[i], base + ws_off[i], it.code, it.n_frames, it.obs, it.channel, schedule,
                                it.prior, max_iter, it.x_hat, it.iters, it.converged, nullptr, method, nullptr, 0);
         if (e != cudaSuccess) {
@@ -654,6 +687,8 @@ extern "C" gfbp_status gfbp_batch_set_variants(gfbp_batch* b, const int32_t* var
         const int q = b->args[i].c.q;
         std::vector<int> ok = b->m.schedule == GFBP_SUS ? sus_candidates(q) : std::vector<int>{default_variant(q)};
         if (b->m.schedule == GFBP_SUS && tensor_variant(q) >= 0) ok.push_back(tensor_variant(q));
+        if (b->m.schedule == GFBP_SUS)
+            for (int t : other_route_variants(q)) ok.push_back(t);
         bool found = false;
         for (int c : ok) found |= (c == variants[i]);
         if (!found) {

@@ -155,19 +155,6 @@ Layout layout(const CodeDev& c, long long F, bool markov, int K, bool step) {
     return l;
 }
 
-int device_sms() {
-    static int sms[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return 1;
-    if (!sms[dev]) {
-        int v = 0;
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        sms[dev] = v > 0 ? v : 1;
-    }
-    return sms[dev];
-}
-
 // Stationary distribution of a row-stochastic matrix (pi T = pi, sum 1), by
 // Gaussian elimination with partial pivoting on (T^T - I) with one row
 // replaced by the normalisation.
@@ -203,6 +190,7 @@ gfbp_status cuda_fail(const char* where, cudaError_t e) {
 
 struct Common {
     bool markov = false;
+    bool gs = false;
     int K = 0;
     std::vector<float> Mt, pi;
     std::vector<int> src_index, src_pos;
@@ -227,7 +215,8 @@ gfbp_status check_common(const char* fn, const gfbp_code* code, int32_t F, const
     }
     if (schedule != GFBP_PUS && schedule != GFBP_SUS) { set_error(w + ": unknown schedule"); return GFBP_EINVAL; }
     const int q = code->dev.q, N = code->dev.N;
-    if (prior && prior->kind == GFBP_PRIOR_MARKOV) {
+    if (prior && (prior->kind == GFBP_PRIOR_MARKOV || prior->kind == GFBP_PRIOR_MARKOV_GS)) {
+        C.gs = prior->kind == GFBP_PRIOR_MARKOV_GS;
         if (!prior->T || prior->K < 1 || prior->K > N) {
             set_error(w + ": Markov prior needs T and 1 <= K <= N");
             return GFBP_EINVAL;
@@ -284,6 +273,7 @@ gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const flo
     A.max_iter = max_iter;
     A.early_stop = (opt && opt->no_early_stop && !step) ? 0 : 1;
     A.markov = C.markov;
+    A.markov_gs = C.gs;
     A.K = C.K;
     A.xhat = x_hat;
     A.iters = iters;
@@ -294,10 +284,6 @@ gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const flo
     A.msg_io = msg_io;
     A.prior_out = prior_out;
     const int m = opt ? opt->check_method : GFBP_CHECK_AUTO;
-    if (m == GFBP_CHECK_DIRECT && c.q > 16) {
-        set_error("check_method DIRECT needs q <= 16");
-        return GFBP_EUNSUPPORTED;
-    }
     if (m < GFBP_CHECK_AUTO || m > GFBP_CHECK_TENSOR) {
         set_error("unknown check_method");
         return GFBP_EINVAL;
@@ -307,10 +293,10 @@ gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const flo
         return GFBP_EUNSUPPORTED;
     }
     A.method = m == GFBP_CHECK_TENSOR ? kTensor
-             : (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > 16)) ? kTransform : kDirect;
+             : (m == GFBP_CHECK_TRANSFORM || (m == GFBP_CHECK_AUTO && c.q > kAutoDirectMaxQ)) ? kTransform : kDirect;
     A.width = opt ? opt->sus_width : 0;
     A.layout = opt ? opt->layout : GFBP_LAYOUT_AUTO;
-    if (A.layout < GFBP_LAYOUT_AUTO || A.layout > GFBP_LAYOUT_THREAD) {
+    if (A.layout < GFBP_LAYOUT_AUTO || A.layout > GFBP_LAYOUT_L2RESIDENT) {
         set_error("unknown layout");
         return GFBP_EINVAL;
     }
@@ -368,6 +354,18 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
         set_error("check_method TENSOR is implemented for SUS only");
         return GFBP_EUNSUPPORTED;
     }
+    if (C.gs && (schedule != GFBP_SUS || step || (A.method == kDirect && c.q > 16) || A.method == kTensor ||
+                 c.dcmax > 16 || c.dvmax > 8)) {
+        set_error("prior MARKOV_GS needs SUS with gfbp_decode and, for q >= 32, check_method TRANSFORM");
+        return GFBP_EUNSUPPORTED;
+    }
+    const bool resident = schedule == GFBP_PUS ? pus_res_eligible(A) : (sus_res_eligible(A, device_sms()) || sus_l2_eligible(A));
+    if ((A.layout == GFBP_LAYOUT_RESIDENT || A.layout == GFBP_LAYOUT_L2RESIDENT) && !resident) {
+        set_error("layouts RESIDENT and L2RESIDENT need the DIRECT check node (q <= 16); RESIDENT a frame whose "
+                  "messages fit in one CTA's shared memory and, for PUS, row degree <= 6 and column degree <= 4; "
+                  "L2RESIDENT is SUS only; both SUS layouts need AUTO or RUNNING partials and the Jacobi prior");
+        return GFBP_EUNSUPPORTED;
+    }
 
     void* ws = opt ? opt->workspace : nullptr;
     bool own = false;
@@ -407,7 +405,8 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(A.work, 0, sizeof(int), stream);
     if (e == cudaSuccess) e = launch_channel(A, stream);
-    if (e == cudaSuccess && schedule == GFBP_SUS) e = launch_init_dev(A, stream);
+    // (the resident kernels initialise their messages in shared memory)
+    if (e == cudaSuccess && schedule == GFBP_SUS && !resident) e = launch_init_dev(A, stream);
     cudaEvent_t ev0 = opt ? static_cast<cudaEvent_t>(opt->kernel_events[0]) : nullptr;
     cudaEvent_t ev1 = opt ? static_cast<cudaEvent_t>(opt->kernel_events[1]) : nullptr;
     if (e == cudaSuccess && ev0) e = cudaEventRecord(ev0, stream);
@@ -450,6 +449,10 @@ cudaError_t batch_prepare_item(DecodeArgs& A, void* ws, const gfbp_code* code, i
                                size_t* ws_bytes, cudaStream_t stream) {
     Common C;
     if (check_common("gfbp_batch_create", code, F, obs, ch, schedule, prior, C) != GFBP_OK) return cudaErrorInvalidValue;
+    if (C.gs) {
+        set_error("gfbp_batch_create: prior MARKOV_GS is decoded by gfbp_decode only");
+        return cudaErrorInvalidValue;
+    }
     if (fill_args(A, code, F, obs, ch, C, max_iter, false, x_hat, iters, conv, nullptr, nullptr, opt) != GFBP_OK)
         return cudaErrorInvalidValue;
     A.method = method;
@@ -471,7 +474,7 @@ extern "C" gfbp_status gfbp_workspace_size(const gfbp_code* code, int32_t n_fram
                                            const gfbp_prior* prior, int32_t step, size_t* bytes) {
     if (!code || !bytes || n_frames < 0) { set_error("gfbp_workspace_size: bad argument"); return GFBP_EINVAL; }
     if (schedule != GFBP_PUS && schedule != GFBP_SUS) { set_error("gfbp_workspace_size: unknown schedule"); return GFBP_EINVAL; }
-    const bool markov = prior && prior->kind == GFBP_PRIOR_MARKOV;
+    const bool markov = prior && (prior->kind == GFBP_PRIOR_MARKOV || prior->kind == GFBP_PRIOR_MARKOV_GS);
     *bytes = layout(code->dev, n_frames, markov, markov ? prior->K : 0, step != 0).total;
     return GFBP_OK;
 }

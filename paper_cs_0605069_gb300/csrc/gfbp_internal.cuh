@@ -72,6 +72,7 @@ struct DecodeArgs {
     int early_stop;
     // Markov block priors (Eqs. 6-7)
     int markov;
+    int markov_gs;         // Markov priors re-estimated inside the SUS sweep (MARKOV_GS)
     int K;
     const float* Mt;       // [q][q] row-normalised transition matrix
     const float* pi;       // [q] stationary distribution
@@ -497,7 +498,7 @@ __device__ __forceinline__ void to_relabelled(float (&x)[Lay<Q>::V], int h, floa
 template <int Q>
 __device__ __forceinline__ void xconv_sm(float (&out)[Lay<Q>::V], const float* sa, const float* sb, int g) {
     constexpr int V = Lay<Q>::V;
-    static_assert(V == 2 || V == 4, "direct route needs V in {2, 4}");
+    static_assert(V == 2 || V == 4 || V == 8, "direct route needs V in {2, 4, 8}");
 #pragma unroll
     for (int v = 0; v < V; v++) out[v] = 0.f;
 #pragma unroll
@@ -518,7 +519,7 @@ template <int Q>
 __device__ __forceinline__ void xconv_sm2(float (&out1)[Lay<Q>::V], float (&out2)[Lay<Q>::V], const float* sa,
                                           const float* sb1, const float* sb2, int g) {
     constexpr int V = Lay<Q>::V;
-    static_assert(V == 2 || V == 4, "direct route needs V in {2, 4}");
+    static_assert(V == 2 || V == 4 || V == 8, "direct route needs V in {2, 4, 8}");
 #pragma unroll
     for (int v = 0; v < V; v++) { out1[v] = 0.f; out2[v] = 0.f; }
 #pragma unroll
@@ -614,6 +615,17 @@ __device__ __forceinline__ void markov_prior(const DecodeArgs& A, int f, int i, 
 // deviation transform (any q).
 enum Method { kDirect = 0, kTransform = 1, kTensor = 2 };
 
+// Largest q for which AUTO takes the probability route (q^2 FMAs per
+// convolution); above it AUTO takes the transform route (q log q).
+constexpr int kAutoDirectMaxQ = 64;
+
+// Per-device launch attributes (launch.cu): raise the kernel's dynamic
+// shared-memory limit to smem on the current device if needed and return its
+// CTAs per SM for (threads, smem) in *occ; thread-safe.
+cudaError_t kernel_prepare(const void* fn, int threads, size_t smem, int* occ);
+int device_sms();          // SMs of the current device
+int device_optin_smem();   // opt-in shared memory per CTA of the current device
+
 cudaError_t launch_channel(const DecodeArgs& A, cudaStream_t s);
 bool sus_team_eligible(const DecodeArgs& A);
 cudaError_t launch_sus_team(const DecodeArgs& A, int num_sms, cudaStream_t s);
@@ -623,6 +635,12 @@ bool sus_level_eligible(const DecodeArgs& A);
 bool sus_level_sm_eligible(const DecodeArgs& A, int num_sms);
 cudaError_t launch_sus_level_sm(const DecodeArgs& A, int num_sms, cudaStream_t s);
 bool pus_regs_eligible(const DecodeArgs& A);
+bool pus_res_eligible(const DecodeArgs& A);
+bool sus_res_eligible(const DecodeArgs& A, int num_sms);
+bool sus_l2_eligible(const DecodeArgs& A);
+cudaError_t launch_sus_l2(const DecodeArgs& A, int num_sms, cudaStream_t s);
+cudaError_t launch_pus_res(const DecodeArgs& A, int num_sms, cudaStream_t s);
+cudaError_t launch_sus_res(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus_level(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus_level_tr(const DecodeArgs& A, int num_sms, cudaStream_t s);
 cudaError_t launch_sus_level_tc(const DecodeArgs& A, int num_sms, cudaStream_t s);

@@ -9,15 +9,10 @@ template <int Q, int DC, int DV, int METHOD, bool BULK>
 cudaError_t launch_qb(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr int G = Lay<Q>::G;
     constexpr size_t smem = sizeof(float) * (size_t)(kPusThreads / G) * pus_group_scratch<Q, DC, METHOD, BULK>();
-    static int occ = -1;
-    if (occ < 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_pus<Q, DC, DV, METHOD, BULK>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus<Q, DC, DV, METHOD, BULK>, kPusThreads, smem);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-    }
+    int occ = 0;
+    cudaError_t e = kernel_prepare((const void*)k_pus<Q, DC, DV, METHOD, BULK>, kPusThreads, smem, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     long long grid = (long long)num_sms * occ;
     if (grid > A.F) grid = A.F;
     if (grid < 1) return cudaSuccess;
@@ -45,9 +40,7 @@ cudaError_t launch_deg(const DecodeArgs& A, int num_sms, cudaStream_t s) {
 
 template <int Q>
 cudaError_t launch_method(const DecodeArgs& A, int num_sms, cudaStream_t s) {
-    if constexpr (Q <= 16) {
-        if (A.method == kDirect) return launch_deg<Q, kDirect>(A, num_sms, s);
-    }
+    if (A.method == kDirect) return launch_deg<Q, kDirect>(A, num_sms, s);
     return launch_deg<Q, kTransform>(A, num_sms, s);
 }
 
@@ -56,21 +49,10 @@ constexpr int kPusRegsThreads = 128;
 template <int Q, int T>
 cudaError_t launch_regs_qt(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     const size_t smem = sizeof(float) * (size_t)(pus_regs_rows(A.c.dcmax, A.c.dvmax) + 1) * T * (Q + 1);
-    static size_t smem_set = 0;   // largest dynamic size enabled so far
-    static int occ_smem = -1;
-    static int occ = 1;
-    cudaError_t e = cudaSuccess;
-    if (smem > smem_set) {
-        e = cudaFuncSetAttribute(k_pus_regs<Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
-    }
-    if ((int)smem != occ_smem) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pus_regs<Q, T>, T, smem);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-        occ_smem = (int)smem;
-    }
+    int occ = 0;
+    cudaError_t e = kernel_prepare((const void*)k_pus_regs<Q, T>, T, smem, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     long long grid = (long long)num_sms * occ;
     if (grid > A.F) grid = A.F;
     if (grid < 1) return cudaSuccess;
@@ -96,6 +78,7 @@ bool pus_regs_eligible(const DecodeArgs& A) {
 // for the lane kernel; GF(8), N = 2000 with a Markov prior, 2048 frames 13.7
 // against 16.8; GF(4), N = 96, 8192 frames 0.93 against 2.66.
 cudaError_t launch_pus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    if (pus_res_eligible(A)) return launch_pus_res(A, num_sms, s);
     const bool thread = A.layout != GFBP_LAYOUT_LANES;
     if (thread && pus_regs_eligible(A)) {
         switch (A.c.q) {

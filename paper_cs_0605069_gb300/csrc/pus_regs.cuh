@@ -58,12 +58,7 @@ __device__ __forceinline__ void gnormalise_regs(float (&x)[Q]) {
 // (the order of xconv_sm).
 template <int Q>
 __device__ __forceinline__ void xconv_chain(float (&out)[Q], const float (&a)[Q], const float (&b)[Q]) {
-#pragma unroll
-    for (int y = 0; y < Q; y++) out[y] = fmaf(a[0], b[y], 0.f);
-#pragma unroll
-    for (int x = 1; x < Q; x++)
-#pragma unroll
-        for (int y = 0; y < Q; y++) out[y] = fmaf(a[x], b[x ^ y], out[y]);
+    xconv_pk<Q>(out, a, b);   // two outputs per packed FMA, each the same chain
 }
 
 template <int Q>

@@ -167,7 +167,7 @@ gfbp_status setup(gfbp_server* S, Req& r) {
     ch.frame_param = r.fparam.empty() ? nullptr : reinterpret_cast<const float*>(base + r.o_fp);
     gfbp_prior pr{};
     if (r.markov) { pr.kind = GFBP_PRIOR_MARKOV; pr.T = r.T.data(); pr.K = r.K; pr.src_pos = r.src_pos.data(); }
-    const int method = r.code->dev.q <= 16 ? kDirect : kTransform;
+    const int method = r.code->dev.q <= kAutoDirectMaxQ ? kDirect : kTransform;
     e = batch_prepare_item(r.A, base + r.o_ws, r.code, r.F, reinterpret_cast<const float*>(base + r.o_obs), ch,
                            (gfbp_schedule)r.schedule, r.markov ? &pr : nullptr, r.max_iter, base + r.o_x,
                            reinterpret_cast<int32_t*>(base + r.o_it), base + r.o_cv, nullptr, method, nullptr,

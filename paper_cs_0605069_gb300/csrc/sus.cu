@@ -9,12 +9,10 @@ template <int Q, int DC, int DV, int METHOD>
 cudaError_t launch_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr int G = Lay<Q>::G;
     constexpr int groups_per_block = kSusThreads / G;
-    static int occ = -1;
-    if (occ < 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus<Q, DC, DV, METHOD>, kSusThreads, 0);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-    }
+    int occ = 0;
+    cudaError_t e = kernel_prepare((const void*)k_sus<Q, DC, DV, METHOD>, kSusThreads, 0, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     long long want = ((long long)A.F + groups_per_block - 1) / groups_per_block;
     long long cap = (long long)num_sms * occ;
     long long grid = want < cap ? want : cap;
@@ -44,11 +42,9 @@ cudaError_t launch_init_q(const DecodeArgs& A, cudaStream_t s) {
     long long blocks = (total + (256 / G) - 1) / (256 / G);
     if (blocks > 65535LL * 16) blocks = 65535LL * 16;
     if (blocks < 1) return cudaSuccess;
-    if constexpr (Q <= 16) {
-        if (A.method == kDirect) {
-            k_init_dev<Q, kDirect><<<(unsigned)blocks, 256, 0, s>>>(A);
-            return cudaGetLastError();
-        }
+    if (A.method == kDirect) {
+        k_init_dev<Q, kDirect><<<(unsigned)blocks, 256, 0, s>>>(A);
+        return cudaGetLastError();
     }
     if constexpr (Q >= 16) {
         if (A.method == kTensor) {
@@ -62,8 +58,30 @@ cudaError_t launch_init_q(const DecodeArgs& A, cudaStream_t s) {
 
 }  // namespace
 
+// The column-walking group kernel for every q (the Gauss-Seidel prior chains
+// the sweep through the source symbols).
+cudaError_t launch_sus_group(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    switch (A.c.q) {
+    case 2: return launch_method<2>(A, num_sms, s);
+    case 4: return launch_method<4>(A, num_sms, s);
+    case 8: return launch_method<8>(A, num_sms, s);
+    case 16: return launch_method<16>(A, num_sms, s);
+    case 32: return launch_method<32>(A, num_sms, s);
+    case 64: return launch_method<64>(A, num_sms, s);
+    case 128: return launch_method<128>(A, num_sms, s);
+    case 256: return launch_method<256>(A, num_sms, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_sus(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     if (A.method == kTensor) return launch_sus_level_tc(A, num_sms, s);
+    if (A.markov_gs) return launch_sus_group(A, num_sms, s);
+    if (sus_res_eligible(A, num_sms)) return launch_sus_res(A, num_sms, s);
+    if (sus_l2_eligible(A)) return launch_sus_l2(A, num_sms, s);
+    // the probability route for q >= 32 runs by levels with a lane group per
+    // pair whatever the layout (no column-walking kernel carries it)
+    if (A.method == kDirect && A.c.q > 16) return launch_sus_level_tr(A, num_sms, s);
     if (A.layout != GFBP_LAYOUT_LANES) {
         if (sus_level_sm_eligible(A, num_sms)) return launch_sus_level_sm(A, num_sms, s);
         if (sus_level_eligible(A)) return launch_sus_level(A, num_sms, s);

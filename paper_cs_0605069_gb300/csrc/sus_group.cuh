@@ -199,12 +199,32 @@ __device__ __forceinline__ void sus_group_frame(const DecodeArgs& A, int f, cons
     }
     int t = t0 + 1, ok = 0;
     bool fin = false;
+    if (A.markov_gs && t0 == 0) {
+        // Gauss-Seidel priors: before its first visit a source symbol's
+        // pseudo-posterior is its initial belief p_j (channel times pi)
+        for (int i = 0; i < A.K; i++) {
+            float x[V];
+            prior_vec<Q>(A, f, A.src_pos[i], x, mask, g);
+            stv<V>(A.Qsrc + ((size_t)f * A.K + i) * Q + g * V, x);
+        }
+        __syncwarp(mask);
+    }
     for (;; t++) {
         ColBuf<Q, PF ? DC : 1, PF ? DV : 1> cur, nxt;
         if constexpr (PF) load_col<Q, DC, DV>(cur, A, slab, 0, g);
         for (int j = 0; j < N; j++) {
             if constexpr (PF) {
                 if (j + 1 < N) load_col<Q, DC, DV>(nxt, A, slab, j + 1, g);
+            }
+            if (A.markov_gs) {
+                // the block prior of a source symbol, re-estimated (Eq. 6) as the
+                // sweep reaches it from its neighbours' current pseudo-posteriors
+                const int si = A.src_index[j];
+                if (si >= 0) {
+                    __syncwarp(mask);   // every lane's part of the latest Q is stored
+                    markov_prior<Q>(A, f, si, A.P + ((size_t)f * A.K + si) * Q, mask, g);
+                    __syncwarp(mask);
+                }
             }
             const int c0 = A.c.colptr[j];
             const int d = A.c.colptr[j + 1] - c0;
@@ -289,7 +309,7 @@ __device__ __forceinline__ void sus_group_frame(const DecodeArgs& A, int f, cons
             fin = true;
             break;
         }
-        if (A.markov) {
+        if (A.markov && !A.markov_gs) {
             for (int i = 0; i < A.K; i++) markov_prior<Q>(A, f, i, A.P + ((size_t)f * A.K + i) * Q, mask, g);
             __syncwarp(mask);
         }

@@ -7,12 +7,10 @@ namespace {
 
 template <int Q, int T, bool RUN>
 cudaError_t launch_level_qr(const DecodeArgs& A, int num_sms, cudaStream_t s) {
-    static int occ = -1;
-    if (occ < 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_level<Q, 8, T, RUN>, T, 0);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-    }
+    int occ = 0;
+    cudaError_t e = kernel_prepare((const void*)k_sus_level<Q, 8, T, RUN>, T, 0, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     const long long cap = (long long)num_sms * occ;
     const long long grid = A.F < cap ? A.F : cap;
     if (grid < 1) return cudaSuccess;

@@ -146,19 +146,66 @@ __device__ __forceinline__ void st_lrow(float* p, const float (&x)[Q]) {
     else stq<Q>(p, x);
 }
 
+// o = U (*) Y: o[y] = fma(U[Q-1], Y[(Q-1)^y], ... fma(U[1], Y[1^y], U[0] Y[y] + 0)),
+// outputs y and y^1 in one packed FMA each step.
+template <int Q>
+__device__ __forceinline__ void xconv_pk(float (&o)[Q], const float (&U)[Q], const float (&Y)[Q]) {
+    float2 acc[Q / 2];
+    const float2 zero = make_float2(0.f, 0.f);
+    {
+        const float2 u = make_float2(U[0], U[0]);
+#pragma unroll
+        for (int k = 0; k < Q / 2; k++) acc[k] = __ffma2_rn(u, make_float2(Y[2 * k], Y[2 * k + 1]), zero);
+    }
+#pragma unroll
+    for (int x = 1; x < Q; x++) {
+        const float2 u = make_float2(U[x], U[x]);
+#pragma unroll
+        for (int k = 0; k < Q / 2; k++) {
+            const int i = x ^ (2 * k);
+            acc[k] = __ffma2_rn(u, make_float2(Y[i], Y[i ^ 1]), acc[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < Q / 2; k++) {
+        o[2 * k] = acc[k].x;
+        o[2 * k + 1] = acc[k].y;
+    }
+}
+
 // U <- U (*) Y, (U (*) Y)[y] = sum_x U[x] Y[x XOR y]: one FMA chain per output
-// in increasing x (the q outputs are independent chains).
+// in increasing x (the q outputs are independent chains), two outputs per
+// packed FMA.
 template <int Q>
 __device__ __forceinline__ void xconv_regs(float (&U)[Q], const float (&Y)[Q]) {
     float o[Q];
-#pragma unroll
-    for (int y = 0; y < Q; y++) o[y] = fmaf(U[0], Y[y], 0.f);
-#pragma unroll
-    for (int x = 1; x < Q; x++)
-#pragma unroll
-        for (int y = 0; y < Q; y++) o[y] = fmaf(U[x], Y[x ^ y], o[y]);
+    xconv_pk<Q>(o, U, Y);
 #pragma unroll
     for (int y = 0; y < Q; y++) U[y] = o[y];
+}
+
+// out[a] = src[z XOR tbl[a]] with tbl a 16-byte-aligned row of Q byte indices
+// (read in one access for q >= 4).
+template <int Q>
+__device__ __forceinline__ void gather_row(float (&out)[Q], const float* src, const uint8_t* tbl, int z) {
+    if constexpr (Q == 16) {
+        const uint4 t = *reinterpret_cast<const uint4*>(tbl);
+        const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int a = 0; a < 16; a++) out[a] = src[z ^ ((w[a >> 2] >> (8 * (a & 3))) & 255)];
+    } else if constexpr (Q == 8) {
+        const uint2 t = *reinterpret_cast<const uint2*>(tbl);
+        const unsigned w[2] = {t.x, t.y};
+#pragma unroll
+        for (int a = 0; a < 8; a++) out[a] = src[z ^ ((w[a >> 2] >> (8 * (a & 3))) & 255)];
+    } else if constexpr (Q == 4) {
+        const unsigned w = *reinterpret_cast<const unsigned*>(tbl);
+#pragma unroll
+        for (int a = 0; a < 4; a++) out[a] = src[z ^ ((w >> (8 * a)) & 255)];
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; a++) out[a] = src[z ^ tbl[a]];
+    }
 }
 
 // Pairwise tree over the index bits, lowest bit first (the order of slot_sum).
@@ -227,8 +274,7 @@ __device__ __forceinline__ void level_check(const DecodeArgs& A, int f, const fl
     // r_ij[a] = s[z XOR h a], normalised
     st_lrow<Q>(row, U);
     float R[Q];
-#pragma unroll
-    for (int a = 0; a < Q; a++) R[a] = row[z ^ s_mul[h * Q + a]];   // both below Q
+    gather_row<Q>(R, row, s_mul + h * Q, z);   // r[a] = s[z XOR h a]
     normalise_regs<Q>(R);
     st_lrow<Q>(row, R);
 }
@@ -267,8 +313,7 @@ __device__ __forceinline__ void level_check_run(const DecodeArgs& A, int f, cons
     }
     st_lrow<Q>(row, U);
     float R[Q];
-#pragma unroll
-    for (int a = 0; a < Q; a++) R[a] = row[z ^ s_mul[h * Q + a]];   // both below Q
+    gather_row<Q>(R, row, s_mul + h * Q, z);   // r[a] = s[z XOR h a]
     normalise_regs<Q>(R);
     st_lrow<Q>(row, R);
 }
@@ -359,8 +404,7 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
     // stored form: qt[y] = q[h^-1 y]
     st_lrow<Q>(orow, other);
     float qt[Q];
-#pragma unroll
-    for (int y = 0; y < Q; y++) qt[y] = orow[s_div[h * Q + y]];
+    gather_row<Q>(qt, orow, s_div + h * Q, 0);
     stq_g<Q>(slab + (size_t)in.x * Q, qt);
     if constexpr (RUN) {
         const int t = in.x - in.y;
@@ -465,8 +509,8 @@ __device__ __forceinline__ void sus_level_frame(const DecodeArgs& A, int f, cons
 template <int Q, int DC, int T, bool RUN>
 __global__ void __launch_bounds__(T, 640 / T) k_sus_level(const DecodeArgs A) {
     static_assert(T % 32 == 0, "whole warps");
-    __shared__ uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a
-    __shared__ uint8_t s_div[Q * Q];   // s_div[h*Q + b] = h^-1 b
+    __shared__ __align__(16) uint8_t s_mul[Q * Q];   // s_mul[h*Q + a] = h a
+    __shared__ __align__(16) uint8_t s_div[Q * Q];   // s_div[h*Q + b] = h^-1 b
     __shared__ __align__(16) float s_row[kLevelPiece * level_rs<Q>()];
     __shared__ __align__(16) float s_orow[T * level_rs<Q>()];
     __shared__ int s_f;

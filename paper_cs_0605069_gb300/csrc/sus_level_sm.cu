@@ -6,18 +6,7 @@ namespace gfbp {
 
 namespace {
 
-int optin_smem() {
-    static int bytes[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return 0;
-    if (!bytes[dev]) {
-        int v = 0;
-        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        bytes[dev] = v > 0 ? v : 1;
-    }
-    return bytes[dev];
-}
+int optin_smem() { return device_optin_smem(); }
 
 // Static shared memory of the kernel besides the dynamic part (tables, frame
 // index) with a margin.
@@ -28,14 +17,8 @@ template <int Q>
 cudaError_t launch_sm_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr int T = SmLay<Q>::T;
     const size_t bytes = level_sm_bytes<Q>(A.c);
-    static size_t set = 0;   // largest dynamic size enabled so far
-    if (bytes > set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sus_level_sm<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        set = bytes;
-    }
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_level_sm<Q>, T, bytes);
+    cudaError_t e = kernel_prepare((const void*)k_sus_level_sm<Q>, T, bytes, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const long long cap = (long long)num_sms * occ;
@@ -60,7 +43,8 @@ bool fits(const DecodeArgs& A) {
 bool sus_level_sm_eligible(const DecodeArgs& A, int num_sms) {
     if (A.method != kDirect) return false;
     const bool want = A.partials == GFBP_PARTIALS_RUNNING ||
-                      (A.partials == GFBP_PARTIALS_AUTO && (long long)A.F <= (long long)num_sms);
+                      (A.partials == GFBP_PARTIALS_AUTO && A.layout == GFBP_LAYOUT_THREAD &&
+                       (long long)A.F <= (long long)num_sms);
     if (!want) return false;
     switch (A.c.q) {
     case 2: return fits<2>(A);

@@ -11,15 +11,10 @@ template <int Q>
 cudaError_t launch_level_tc_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr int T = kLevelTcThreads;
     constexpr size_t smem = TcLay<Q, T>::total;
-    static int occ = -1;
-    if (occ < 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_sus_level_tc<Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_level_tc<Q, T>, T, smem);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-    }
+    int occ = 0;
+    cudaError_t e = kernel_prepare((const void*)k_sus_level_tc<Q, T>, T, smem, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     const long long cap = (long long)num_sms * occ;
     const long long grid = A.F < cap ? A.F : cap;
     if (grid < 1) return cudaSuccess;

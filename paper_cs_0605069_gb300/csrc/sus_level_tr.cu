@@ -8,24 +8,29 @@ namespace {
 
 constexpr int kLevelTrThreads = 256;
 
-template <int Q>
-cudaError_t launch_level_tr_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+template <int Q, int METHOD>
+cudaError_t launch_level_tr_qm(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr int T = kLevelTrThreads;
     constexpr size_t smem = level_tr_smem<Q, T>();
-    static int occ = -1;
-    if (occ < 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_sus_level_tr<Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_level_tr<Q, T>, T, smem);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-    }
+    int occ = 0;
+    cudaError_t e = kernel_prepare((const void*)k_sus_level_tr<Q, T, METHOD>, T, smem, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     const long long cap = (long long)num_sms * occ;
     const long long grid = A.F < cap ? A.F : cap;
     if (grid < 1) return cudaSuccess;
-    k_sus_level_tr<Q, T><<<(int)grid, T, smem, s>>>(A);
+    k_sus_level_tr<Q, T, METHOD><<<(int)grid, T, smem, s>>>(A);
     return cudaGetLastError();
+}
+
+// The probability route by lane groups is instantiated for q >= 32 (below, the
+// register kernels of sus_level.cuh and resident.cuh run it).
+template <int Q>
+cudaError_t launch_level_tr_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    if constexpr (Q >= 32) {
+        if (A.method == kDirect) return launch_level_tr_qm<Q, kDirect>(A, num_sms, s);
+    }
+    return launch_level_tr_qm<Q, kTransform>(A, num_sms, s);
 }
 
 }  // namespace

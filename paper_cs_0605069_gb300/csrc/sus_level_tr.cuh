@@ -1,6 +1,7 @@
-// SUS (Sec. 2) by levels of the column order with the transform route of the
-// check node (any q; the route used for q >= 32), one lane group per
-// (column, check) pair.
+// SUS (Sec. 2) by levels of the column order with a lane group per (column,
+// check) pair: the transform route of the check node (any q), or the
+// probability route by shared-memory XOR-convolutions (the route AUTO takes
+// for q >= 32, where the q <= 16 register kernels do not apply).
 //
 // The level schedule is the one of sus_level.cuh: the columns of a level share
 // no check, so updating a level's columns at once gives every column the
@@ -9,11 +10,14 @@
 // at most SUB pairs so that its r-vectors fit in shared memory:
 //   step 1  group <-> pair (j, k): the check's other stored deviation vectors
 //           combined (E <- E + D (1 - E)), inverted to r_kj (dev_finish_n) and
-//           kept in a shared row;
+//           kept in a shared row; probability route: the check's other stored
+//           relabelled messages folded by XOR-convolutions in the order of
+//           their positions (the first one is the start), relabelled and
+//           normalised (direct_finish_n);
 //   step 2  after a barrier, group <-> pair (j, k): q_kj from p_j and the
 //           column's other rows, in the product order of sus_column_tail (and
 //           on slot 0, Q_j, the hard decision, the posterior), brought to the
-//           stored deviation form and written to the slab.
+//           stored form of the route and written to the slab.
 // Each step calls the lane-group kernel's own routines on one vector at a
 // time, so the two kernels give the same bits.
 #pragma once
@@ -30,7 +34,7 @@ constexpr int level_tr_sub() {
     return (32768 / (Q * 4)) < kLevelPiece ? (32768 / (Q * 4)) : kLevelPiece;
 }
 
-template <int Q>
+template <int Q, int METHOD>
 __device__ __forceinline__ void level_tr_check(const DecodeArgs& A, const float* slab, const uint8_t* zf, int2 pr,
                                                float* row, float* sc, unsigned mask, int g, const uint8_t* ex,
                                                const uint8_t* lg) {
@@ -45,6 +49,30 @@ __device__ __forceinline__ void level_tr_check(const DecodeArgs& A, const float*
     int C[1] = {0};
     const int h[1] = {(in.z >> 8) & 255};
     const int z[1] = {zf ? (zf[in.w] & (Q - 1)) : 0};
+    if constexpr (METHOD == kDirect) {
+        bool started = false;
+#pragma unroll 1
+        for (int m = 0; m < dc; m++) {
+            if (m == own) continue;
+            const float* Y = slab + (size_t)(in.y + m) * Q;
+            if (!started) {
+                ldv<V>(E[0], Y + g * V);
+                started = true;
+            } else {
+                stv<V>(sc + g * V, E[0]);
+                __syncwarp(mask);
+                xconv_sm<Q>(E[0], sc, Y, g);
+                __syncwarp(mask);
+            }
+        }
+        if (!started) {   // a check of degree 1: the XOR-sum of no other edges is 0
+#pragma unroll
+            for (int v = 0; v < V; v++) E[0][v] = (g * V + v) == 0 ? 1.f : 0.f;
+        }
+        direct_finish_n<Q, 1>(E, h, z, 1, sc, mask, g, ex, lg);
+        stv<V>(row + g * V, E[0]);
+        return;
+    }
 #pragma unroll
     for (int v = 0; v < V; v++) E[0][v] = 0.f;
 #pragma unroll 1
@@ -63,7 +91,7 @@ __device__ __forceinline__ void level_tr_check(const DecodeArgs& A, const float*
     stv<V>(row + g * V, E[0]);
 }
 
-template <int Q>
+template <int Q, int METHOD>
 __device__ __forceinline__ void level_tr_var(const DecodeArgs& A, int f, float* slab, uint8_t* xh, int2 pr,
                                              const float* rows0, float* sc, unsigned mask, int g, const uint8_t* ex,
                                              const uint8_t* lg) {
@@ -125,11 +153,12 @@ __device__ __forceinline__ void level_tr_var(const DecodeArgs& A, int f, float* 
     gnormalise<Q>(x[0], mask);
     if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + in.x) * Q + g * V, x[0]);
     const int h[1] = {(in.z >> 8) & 255};
-    to_deviation_n<Q, 1>(x, h, 1, sc, mask, g, ex, lg);
+    if constexpr (METHOD == kDirect) to_relabelled_n<Q, 1>(x, h, 1, sc, mask, g, ex, lg);
+    else to_deviation_n<Q, 1>(x, h, 1, sc, mask, g, ex, lg);
     stv<V>(slab + (size_t)in.x * Q + g * V, x[0]);
 }
 
-template <int Q, int T>
+template <int Q, int T, int METHOD = kTransform>
 __device__ __forceinline__ void sus_level_tr_frame(const DecodeArgs& A, int f, const uint8_t* s_exp,
                                                    const uint8_t* s_log, float* s_rows, float* sc) {
     constexpr int G = Lay<Q>::G, NG = T / G, SUB = level_tr_sub<Q>();
@@ -160,11 +189,11 @@ __device__ __forceinline__ void sus_level_tr_frame(const DecodeArgs& A, int f, c
                 while (e < pe && A.c.lpair[e].y != 0) e--;
                 const int n = e - s;
                 for (int lp = grp; lp < n; lp += NG)
-                    level_tr_check<Q>(A, slab, zf, A.c.lpair[s + lp], s_rows + (size_t)lp * Q, sc, mask, g, s_exp,
+                    level_tr_check<Q, METHOD>(A, slab, zf, A.c.lpair[s + lp], s_rows + (size_t)lp * Q, sc, mask, g, s_exp,
                                       s_log);
                 __syncthreads();
                 for (int lp = grp; lp < n; lp += NG)
-                    level_tr_var<Q>(A, f, slab, xh, A.c.lpair[s + lp], s_rows + (size_t)lp * Q, sc, mask, g, s_exp,
+                    level_tr_var<Q, METHOD>(A, f, slab, xh, A.c.lpair[s + lp], s_rows + (size_t)lp * Q, sc, mask, g, s_exp,
                                     s_log);
                 __syncthreads();
                 s = e;
@@ -211,7 +240,7 @@ __device__ __forceinline__ void sus_level_tr_frame(const DecodeArgs& A, int f, c
 
 // Dynamic shared memory: SUB rows of Q floats, then one Q-float scratch
 // (+ padding) per lane group.
-template <int Q, int T>
+template <int Q, int T, int METHOD>
 __global__ void __launch_bounds__(T) k_sus_level_tr(const DecodeArgs A) {
     constexpr int G = Lay<Q>::G, SUB = level_tr_sub<Q>();
     __shared__ uint8_t s_exp[512];
@@ -229,7 +258,7 @@ __global__ void __launch_bounds__(T) k_sus_level_tr(const DecodeArgs A) {
         __syncthreads();
         const int f = s_f;
         if (f >= A.F) break;
-        sus_level_tr_frame<Q, T>(A, f, s_exp, s_log, s_rows, sc);
+        sus_level_tr_frame<Q, T, METHOD>(A, f, s_exp, s_log, s_rows, sc);
     }
 }
 

@@ -8,12 +8,10 @@ namespace {
 template <int Q, int DC>
 cudaError_t launch_team_q(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr int teams_per_block = kTeamThreads / TeamLay<Q>::TEAM;
-    static int occ = -1;
-    if (occ < 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sus_team<Q, DC>, kTeamThreads, 0);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-    }
+    int occ = 0;
+    cudaError_t e = kernel_prepare((const void*)k_sus_team<Q, DC>, kTeamThreads, 0, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     long long want = ((long long)A.F + teams_per_block - 1) / teams_per_block;
     long long cap = (long long)num_sms * occ;
     long long grid = want < cap ? want : cap;

@@ -11,12 +11,7 @@ void set_error(const std::string& msg);
 
 namespace {
 
-int sm_count() {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    return v > 0 ? v : 1;
-}
+int sm_count() { return device_sms(); }
 
 template <int Q>
 __global__ void __launch_bounds__(256) k_wht_simt(const float* __restrict__ x, float* __restrict__ y, long long n) {
@@ -103,14 +98,10 @@ cudaError_t launch_wht(const float* x, float* y, long long n, int method, cudaSt
     }
     if constexpr (Q >= 16) {
         constexpr size_t smem = tc_smem<Q>();
-        static int occ = -1;
-        if (occ < 0) {
-            cudaError_t e = cudaFuncSetAttribute(k_wht_tc<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wht_tc<Q>, 256, smem);
-            if (e != cudaSuccess) return e;
-            if (occ < 1) occ = 1;
-        }
+        int occ = 0;
+        cudaError_t e = kernel_prepare((const void*)k_wht_tc<Q>, 256, smem, &occ);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
         long long blocks = (n + kTcRows - 1) / kTcRows;
         const long long cap = (long long)sm_count() * occ;
         if (blocks > cap) blocks = cap;

@@ -22,7 +22,7 @@ GFBP_OK, GFBP_EINVAL, GFBP_ENOMEM, GFBP_ECUDA, GFBP_ETIMEOUT, GFBP_EBUSY, GFBP_E
 CHANNEL = {"bsc": 0, "bec": 1, "awgn": 2, "biawgn": 2, "loglik": 3}
 SCHEDULE = {"pus": 0, "sus": 1}
 CHECK_METHOD = {"auto": 0, "transform": 1, "direct": 2, "tensor": 3}
-LAYOUT = {"auto": 0, "lanes": 1, "thread": 2}
+LAYOUT = {"auto": 0, "lanes": 1, "thread": 2, "resident": 3, "l2resident": 4}
 PARTIALS = {"auto": 0, "fold": 1, "running": 2, "running_global": 3}
 
 # Functions declared in include/gfbp.h (the CPU test checks that every one is exported).
@@ -163,12 +163,12 @@ def _stream(stream):
     return C.c_void_p(s.cuda_stream)
 
 
-def _prior(T, K, src_pos):
+def _prior(T, K, src_pos, gauss_seidel=False):
     if T is None:
         return gfbp_prior(0, None, 0, None), None
     T = np.ascontiguousarray(T, dtype=np.float64)
     sp = None if src_pos is None else np.ascontiguousarray(src_pos, dtype=np.int32)
-    pr = gfbp_prior(1, T.ctypes.data, int(K), None if sp is None else sp.ctypes.data)
+    pr = gfbp_prior(2 if gauss_seidel else 1, T.ctypes.data, int(K), None if sp is None else sp.ctypes.data)
     return pr, (T, sp)
 
 
@@ -185,7 +185,7 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
            T=None, K: int = 0, src_pos=None, frame_param=None, punct=None, syndrome=None, post: bool = False,
            trace: bool = False, no_early_stop: bool = False, workspace=None, out=None, stream=None,
            kernel_events=None, check_method: str = "auto", sus_width: int = 0,
-           layout: str = "auto", partials: str = "auto"):
+           layout: str = "auto", partials: str = "auto", gauss_seidel: bool = False):
     """gfbp_decode on CUDA tensors.  obs: float32 [F][N][p] (or [F][N][q] for
     loglik).  Returns dict of device tensors x_hat [F][N] uint8, iters [F]
     int32, converged [F] uint8 (+ post [F][N][q], trace [F][max_iter][N]).
@@ -193,7 +193,8 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
     direct check node, same results); sus_width: SUS lane teams per frame of
     the "lanes" layout (0 = automatic); partials: "auto", "fold", "running" or
     "running_global" (how the SUS level kernel gathers a check's other
-    messages)."""
+    messages); gauss_seidel: with a Markov source (T), re-estimate each block
+    prior as the SUS sweep reaches it (prior kind MARKOV_GS)."""
     import torch
     F = int(obs.shape[0])
     dev = obs.device
@@ -205,7 +206,7 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
             out["post"] = torch.empty((F, code.N, code.q), dtype=torch.float32, device=dev)
         if trace:
             out["trace"] = torch.empty((F, max_iter, code.N), dtype=torch.uint8, device=dev)
-    pr, _keep = _prior(T, K, src_pos)
+    pr, _keep = _prior(T, K, src_pos, gauss_seidel)
     if workspace is None:
         nbytes = workspace_size(code, F, schedule, T, K, src_pos)
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)

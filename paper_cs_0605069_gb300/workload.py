@@ -512,3 +512,48 @@ def make_batch(name: str, frames: int | None = None, first_frame: int = 0, N: in
             params[i] = sig
             obs[i] = biawgn(r, x[i:i + 1], p, sig)[0]
     return Batch(code, x, obs, w["channel"], params, T, code.K if T is not None else 0, w["max_iter"])
+
+
+# ---------------------------------------------------------------------------
+# The MN form of Sec. 2 (Eqs. 1-2): H = [A | B] with the source symbols s on
+# the first K columns and B (the last M columns) invertible; the sender
+# transmits t = B^-1 A s, the channel adds noise n (r = t + n on the bits),
+# and the receiver decodes the unknowns w = [s; n] from the syndrome
+# z = H [0; r] = B r, with the source columns never observed (punctured) and
+# a block prior on them, the noise columns carrying the noise prior.
+@dataclass
+class MNBatch:
+    code: Code
+    s: np.ndarray          # [F, K] source words
+    n: np.ndarray          # [F, M] noise symbols (r = t XOR n)
+    obs: np.ndarray        # [F, N, p] decoder observations: 0 bits on the noise columns
+    punct: np.ndarray      # [N] 1 on the source columns
+    z: np.ndarray          # [F, M] syndromes B r
+    f: float               # BSC flip rate of the noise bits
+    T: np.ndarray          # Markov transition matrix of the source
+    K: int
+    max_iter: int
+
+
+def mn_batch(q: int, M: int, frames: int, f: float, stay: float = 0.8, dv: int = 3, dc: int = 6,
+             cfg: str = "mn", max_iter: int = 100) -> MNBatch:
+    """Frames of the MN form over a systematic regular code (N = K + M, source
+    first): a stationary Markov source (self-transition `stay`) and a BSC of
+    flip rate f on the bits of t."""
+    N = M * dc // (dc - dv) if dc != dv else 2 * M
+    code = regular_code(q, N, dv=dv, dc=dc, cfg=cfg)
+    K, p = code.K, code.p
+    T = self_transition_chain(q, stay)
+    u = np.stack([rng_for(cfg, "src", i).random(K) for i in range(frames)])
+    s = markov_source(u, T)
+    x = encode(code, s)
+    t = x[:, K:].astype(np.int64)
+    nb = np.stack([(rng_for(cfg, "noise", i).random((code.M, p)) < f) for i in range(frames)]).astype(np.int64)
+    n = from_bits(nb)
+    r = t ^ n
+    w = np.concatenate([np.zeros((frames, K), np.int64), r], axis=1)
+    z = code.syndrome(w)
+    obs = np.zeros((frames, code.N, p), np.float32)   # the noise prior: bits observed as 0 through BSC(f)
+    punct = np.zeros(code.N, np.uint8)
+    punct[:K] = 1
+    return MNBatch(code, s, n, obs, punct, z.astype(np.uint8), f, T, K, max_iter)

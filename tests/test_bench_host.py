@@ -40,6 +40,8 @@ def test_profiled_traffic_is_gated_on_the_kernels_sources(bench, tmp_path, monke
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"k<16>": entry}))
     assert bench.profiled_traffic("k<16>", 2.0e6) == pytest.approx(1.0e9)
     assert bench.profiled_traffic("other<16>", 2.0e6) is None
+    src.write_text("kernel v1 // a note\n/* and a block */\n")   # comments only: the code is the same
+    assert bench.profiled_traffic("k<16>", 2.0e6) == pytest.approx(1.0e9)
     src.write_text("kernel v2\n")        # the kernel changed since the counters were taken
     assert bench.profiled_traffic("k<16>", 2.0e6) is None
 
@@ -50,9 +52,23 @@ def test_committed_profiles_cover_the_benchmark_kernels(bench):
         assert name in t, name
     for name, ent in t.items():
         assert re.fullmatch(r"[0-9a-f]{16}", ent["source_hash"]), name
+        # the counters were taken on the code the files hold now
+        assert bench.files_hash(ent["files"]) == ent["source_hash"], f"{name}: profile is stale"
         assert ent["dram_bytes_per_symiter"] > 0
         for f in ent["files"]:
             assert os.path.exists(os.path.join(ROOT, f)), f
         assert os.path.exists(os.path.join(ROOT, ent["capture"])), ent["capture"]
         text = open(os.path.join(ROOT, ent["capture"])).read()
         assert "ncu" in text and "--clock-control none" in text
+
+
+def test_error_rates_by_noise_level(bench):
+    import numpy as np
+    x = np.zeros((6, 4), np.int64)
+    xh = x.copy()
+    xh[1, 0] = 3          # level 1.5 dB: one symbol, two bits wrong
+    xh[3, :] = 1          # level 1.0 dB: a whole frame, one bit per symbol
+    r = bench.error_rates(xh, x, 4)
+    assert r["1.0"] == {"fer": 0.5, "ser": 0.5, "ber": 4 / 16, "frames": 2}
+    assert r["1.5"] == {"fer": 0.5, "ser": 1 / 8, "ber": 2 / 16, "frames": 2}
+    assert r["2.0"]["fer"] == 0.0 and r["all"]["frames"] == 6

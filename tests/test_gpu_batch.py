@@ -1,6 +1,13 @@
 """Batched decoding (one persistent launch over frames of several codes with
-uneven q and N) against gfbp_decode of each code alone, CUDA-graph replay of a
-batch run, and the autotuner."""
+uneven q and N) against the FP64 oracle item by item and against gfbp_decode
+of each code alone in the same kernel routine, CUDA-graph replay of a batch
+run, and the autotuner.
+
+Batch items run the level kernels that fold a check's messages per visit
+(q <= 16) or the lane-group level kernels (q >= 32), and the lane-group PUS
+routine; gfbp_decode's AUTO takes the frame-resident kernels for q <= 16,
+whose SUS arithmetic (running partial convolutions) rounds differently, so
+the bit-for-bit comparisons decode alone with partials FOLD."""
 import numpy as np
 import pytest
 
@@ -16,7 +23,7 @@ def env():
     return torch, gfbp, W
 
 
-def _mixed_items(torch, gfbp, W, frames=24):
+def _mixed_items(torch, gfbp, W, frames=24, keep_host=False):
     """Codes with q in {2, 4, 16, 64, 256} and uneven N, BI-AWGN at 1.5 dB,
     noisy all-zero or random codewords (the channel is symmetric)."""
     items, refs = [], []
@@ -29,7 +36,13 @@ def _mixed_items(torch, gfbp, W, frames=24):
         obs = torch.from_numpy(W.biawgn(rng, x, code.p, sig)).cuda()
         cd = gfbp.Code.from_coo(code)
         items.append(dict(code=cd, obs=obs, channel="awgn", param=sig))
+        if keep_host:
+            items[-1]["host"] = (code, obs.cpu().numpy())
     return items
+
+
+def _alone_kw(q, schedule):
+    return dict(partials="fold") if schedule == "sus" and q <= 16 else {}
 
 
 @pytest.mark.parametrize("schedule", ["pus", "sus"])
@@ -40,10 +53,35 @@ def test_batch_equals_each_code_alone(env, schedule):
     outs = b.run()
     torch.cuda.synchronize()
     for it, o in zip(items, outs):
-        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule=schedule, max_iter=40)
+        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule=schedule, max_iter=40,
+                          **_alone_kw(it["code"].q, schedule))
         torch.cuda.synchronize()
         for k in ("x_hat", "iters", "converged"):
             assert torch.equal(ref[k], o[k]), (it["code"].q, k)
+    b.close()
+
+
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_batch_items_against_the_oracle(env, oracle, schedule):
+    """Every frame of every item of a mixed batch (q in {2, 4, 16, 64, 256})
+    against the FP64 oracle's decode of that item (Sec. 2): identical
+    decisions, counts and flags except tie and horizon frames."""
+    from tests.parity_util import classify_final, oracle_horizon
+    torch, gfbp, W = env
+    items = _mixed_items(torch, gfbp, W, frames=24, keep_host=True)
+    b = gfbp.Batch(items, schedule=schedule, max_iter=40)
+    outs = b.run()
+    torch.cuda.synchronize()
+    for it, o in zip(items, outs):
+        code, obs = it["host"]
+        ora = oracle.decode(code, obs, "awgn", it["param"], schedule, max_iter=40, trace=True)
+        hz = oracle_horizon(oracle, code, obs, "awgn", it["param"], schedule, 40)
+        g = {k: v.cpu().numpy() for k, v in o.items()}
+        kinds = classify_final(g, ora, horizon=hz)
+        n = {k: int((kinds == k).sum()) for k in ("match", "tie", "horizon", "fail")}
+        print(f"batch {schedule} q={code.q} N={code.N}: {n}")
+        assert n["fail"] == 0, (code.q, np.nonzero(kinds == "fail")[0])
+        assert n["horizon"] <= 0.05 * len(kinds) + 1
     b.close()
 
 
@@ -108,7 +146,9 @@ def test_batch_rejects_bad_items(env):
 TEAM = {4: 0, 8: 1, 16: 2}
 GROUP_D = {2: 3, 4: 4, 8: 5, 16: 6}
 GROUP_T = {32: 7, 64: 8, 128: 9, 256: 10}
-LEVEL = {2: 11, 4: 12, 8: 13, 16: 14, 32: 15, 64: 16, 128: 17, 256: 18}
+LEVEL_T = {32: 15, 64: 16, 128: 17, 256: 18}
+# AUTO's route: the probability route up to q = 64, the transform route above
+LEVEL = {2: 11, 4: 12, 8: 13, 16: 14, 32: 24, 64: 25, 128: 17, 256: 18}
 
 
 def test_batch_default_variants_are_level_schedules(env):
@@ -135,8 +175,11 @@ def test_batch_with_both_kernel_families_equals_each_code_alone(env):
     outs = b.run()
     torch.cuda.synchronize()
     for it, o in zip(items, outs):
-        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule="sus", max_iter=40,
-                          layout="lanes" if it["code"].q == 4 else "auto")
+        q = it["code"].q
+        kw = dict(layout="lanes") if q == 4 else _alone_kw(q, "sus")
+        if q == 64:
+            kw = dict(layout="lanes", check_method="transform")   # the group kernel, transform route
+        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule="sus", max_iter=40, **kw)
         torch.cuda.synchronize()
         for k in ("x_hat", "iters", "converged"):
             assert torch.equal(ref[k], o[k]), (it["code"].q, k)
@@ -158,8 +201,8 @@ def test_batch_tensor_route_variants_equal_decode(env):
     torch.cuda.synchronize()
     for it, o in zip(items, outs):
         q = it["code"].q
-        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule="sus", max_iter=30,
-                          check_method="tensor" if q in (64, 256) else "auto")
+        kw = dict(check_method="tensor") if q in (64, 256) else _alone_kw(q, "sus")
+        ref = gfbp.decode(it["code"], it["obs"], "awgn", it["param"], schedule="sus", max_iter=30, **kw)
         torch.cuda.synchronize()
         for k in ("x_hat", "iters", "converged"):
             assert torch.equal(ref[k], o[k]), (q, k)

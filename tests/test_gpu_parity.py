@@ -3,21 +3,23 @@ the same seeded inputs.
 
 Lock-step: from the oracle's message state at iteration t, one device
 iteration must give the oracle's Q (Eq. 5), q (Eq. 4) and block priors
-(Eqs. 6-7) within LOCKSTEP_ATOL max-abs (probability-domain check node; the
-transform check node keeps an absolute error of ~1e-7 of each message's
-largest entry, which conflicts between checks and channel can amplify, and
-SUS compounds over a sweep, so it is held to TRANSFORM_ATOL: measured maxima
-1.4e-5 (PUS, GF(4), iteration 10) and 4.4e-4 (SUS, GF(16), iteration 6)).  Free-running: decided symbols, iteration counts
-and converged flags identical on every frame except tie frames (every
-disagreement on a symbol with oracle top-two gap <= TIE_GAP) and frames that
-run past their conditioning horizon (see parity_util.oracle_horizon); both
-kinds are counted and reported.
+(Eqs. 6-7) within LOCKSTEP_ATOL = 1e-5 max-abs on the default path (AUTO:
+the probability-domain check node for every q).  The transform check node is
+an explicit, non-default route: it keeps an absolute error of ~1e-7 of each
+message's largest entry, which conflicts between checks and channel can
+amplify and SUS compounds over a sweep; its tests hold it to the accuracy the
+header states for it (TRANSFORM_ATOL).  Free-running: decided symbols,
+iteration counts and converged flags identical on every frame except tie
+frames (every disagreement on a symbol with oracle top-two gap <= TIE_GAP) and
+frames that run past their conditioning horizon at FP32 rounding scale (see
+parity_util.oracle_horizon); both kinds are counted and reported.
 """
 import numpy as np
 import pytest
 
 from tests.parity_util import LOCKSTEP_ATOL, TIE_GAP, classify_frames, gpu_decode, oracle_horizon, to_dev
 
+# The transform route's stated accuracy (not the default path's bar).
 TRANSFORM_ATOL = {"pus": 1e-4, "sus": 1e-3}
 
 
@@ -43,7 +45,7 @@ def _workload(name, frames, N=None):
 
 
 def _lockstep(torch_cuda, oracle, code, obs, kind, param, schedule, iters, T=None, K=0, atol=LOCKSTEP_ATOL,
-              method="auto", layout="auto"):
+              method="auto", layout="auto", syn=None):
     import torch
     from paper_cs_0605069_gb300 import gfbp
     cd = gfbp.Code.from_coo(code)
@@ -56,11 +58,11 @@ def _lockstep(torch_cuda, oracle, code, obs, kind, param, schedule, iters, T=Non
     fp = to_dev(np.broadcast_to(np.asarray(param, np.float32), (F,)).copy())
     worst = 0.0
     for t in range(iters):
-        ref = oracle.step(code, obs, kind, param, msg, schedule, T=T, K=K, prior=prior)
+        ref = oracle.step(code, obs, kind, param, msg, schedule, T=T, K=K, prior=prior, syn=syn)
         m = to_dev(msg.astype(np.float32))
         out = gfbp.step(cd, to_dev(obs, torch.float32), m, channel=kind, schedule=schedule, T=T, K=K,
                         prior_in=None if prior is None else to_dev(prior.astype(np.float32)), frame_param=fp,
-                        check_method=method, layout=layout)
+                        check_method=method, layout=layout, syndrome=None if syn is None else to_dev(syn))
         torch.cuda.synchronize()
         post = out["post"].cpu().numpy()
         dpost = np.abs(post - ref["post"]).max()
@@ -101,6 +103,16 @@ def test_lockstep_gf16_n1000_awgn(torch_cuda, oracle, schedule, method):
               atol=_atol(method, schedule))
 
 
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_lockstep_benchmark_kernels_many_frames(torch_cuda, oracle, schedule):
+    """The benchmark's own kernels (AUTO at GF(16), N = 1000: the frame-resident
+    kernels, whatever the frame count) with more frames than SMs, so CTAs decode
+    several frames in turn: 10 iterations within 1e-5 of the oracle."""
+    b = _workload("gf16_n1000_awgn", 320)
+    worst = _lockstep(torch_cuda, oracle, b.code, b.obs, "awgn", b.param, schedule, iters=10)
+    print(f"{schedule}: worst lock-step deviation over 320 frames x 10 iterations {worst:.2e}")
+
+
 @pytest.mark.parametrize("method", METHODS)
 @pytest.mark.parametrize("schedule", ["pus", "sus"])
 def test_lockstep_gf8_markov(torch_cuda, oracle, schedule, method):
@@ -110,19 +122,35 @@ def test_lockstep_gf8_markov(torch_cuda, oracle, schedule, method):
 
 
 def _free_running(oracle, b, kind, schedule, method="auto", max_horizon_frac=0.05):
+    from tests.parity_util import HORIZON_REL, HORIZON_REL_TRANSFORM
     from paper_cs_0605069_gb300 import gfbp
     cd = gfbp.Code.from_coo(b.code)
     T = b.T
     K = b.K
     ora = oracle.decode(b.code, b.obs, kind, b.param, schedule, max_iter=b.max_iter, T=T, K=K, trace=True)
-    hz = oracle_horizon(oracle, b.code, b.obs, kind, b.param, schedule, b.max_iter, T=T, K=K)
+    rel = HORIZON_REL_TRANSFORM if method == "transform" else HORIZON_REL
+    hz = oracle_horizon(oracle, b.code, b.obs, kind, b.param, schedule, b.max_iter, T=T, K=K, rel=rel)
     gpu = gpu_decode(cd, b.obs, kind, b.param, schedule, b.max_iter, T=T, K=K, trace=True, check_method=method)
     kinds = classify_frames(gpu, ora, horizon=hz)
     n = {k: int((kinds == k).sum()) for k in ("match", "tie", "horizon", "fail")}
     print(f"{schedule}/{method}: frames {len(kinds)} {n}")
-    assert n["fail"] == 0, np.nonzero(kinds == "fail")[0][:10]
+    assert n["fail"] == 0, _fail_report(gpu, ora, hz, np.nonzero(kinds == "fail")[0][:5])
     assert n["horizon"] <= max_horizon_frac * len(kinds) + 1
     return kinds
+
+
+def _fail_report(gpu, ora, hz, frames):
+    """Where each failing frame first left the oracle's decisions on a firm symbol."""
+    out = []
+    for f in frames:
+        t = int(min(gpu["iters"][f], ora["iters"][f]))
+        dis = gpu["trace"][f, :t] != ora["trace_x"][f, :t]
+        firm = dis & (ora["trace_gap"][f, :t] > TIE_GAP)
+        it = np.nonzero(firm.any(1))[0]
+        first = int(it[0]) + 1 if it.size else None
+        out.append(f"frame {f}: iters gpu {gpu['iters'][f]} oracle {ora['iters'][f]}, horizon {hz[f]}, "
+                   f"first firm disagreement at iteration {first}")
+    return "; ".join(out)
 
 
 @pytest.mark.parametrize("schedule", ["pus", "sus"])
@@ -159,13 +187,19 @@ def sampled_parity(oracle, b, kind, schedule, gpu, frames):
     return classify_frames(g, ora, horizon=hz)
 
 
-# The benchmark's launch: 4096 frames of GF(16), N = 1000 at 1.0/1.5/2.0 dB,
-# max 200 iterations, AUTO kernels (SUS: the 64-thread level kernel that
-# folds per visit; PUS: the thread layout).  Frames spread over the batch and
-# the three noise levels are decoded by the oracle one by one.  The horizon
-# share of a batch is bounded by the smaller free-running tests; on a sample
-# of this size only failures are ruled out, and most frames must match.
-BENCH_SAMPLE = [0, 1, 2, 683, 1024, 1366, 2047, 2048, 2730, 3413, 4093, 4094, 4095]
+# The benchmark's launch: 4096 frames of GF(16), N = 1000 at 1.0/1.5/2.0 dB
+# (frame f at the (f mod 3)-th level), max 200 iterations, AUTO kernels.  The
+# oracle decodes 132 frames spread over the batch, 44 at each noise level, one
+# by one: no frame may fail; ties and horizon frames are counted, the latter
+# capped as in the free-running tests.
+_BASES = np.linspace(0, 4093, 44).astype(int) // 3 * 3
+BENCH_SAMPLE = sorted(int(b) + r for b in _BASES for r in range(3))
+
+
+def test_benchmark_sample_spans_the_batch_and_noise_levels():
+    f = np.asarray(BENCH_SAMPLE)
+    assert len(f) == 132 and f.min() == 0 and f.max() >= 4090
+    assert all(int((f % 3 == r).sum()) == 44 for r in range(3))
 
 
 @pytest.mark.parametrize("schedule", ["pus", "sus"])
@@ -176,9 +210,9 @@ def test_benchmark_configuration_sampled_frames(torch_cuda, oracle, schedule):
     gpu = gpu_decode(cd, b.obs, "awgn", b.param, schedule, b.max_iter, trace=True)
     kinds = sampled_parity(oracle, b, "awgn", schedule, gpu, BENCH_SAMPLE)
     n = {k: int((kinds == k).sum()) for k in ("match", "tie", "horizon", "fail")}
-    print(f"{schedule} benchmark configuration, sampled frames: {n}")
+    print(f"{schedule} benchmark configuration, {len(BENCH_SAMPLE)} sampled frames: {n}")
     assert n["fail"] == 0, np.asarray(BENCH_SAMPLE)[kinds == "fail"]
-    assert n["match"] >= len(BENCH_SAMPLE) // 2
+    assert n["horizon"] <= 0.05 * len(BENCH_SAMPLE) + 1
 
 
 # ---------------------------------------------------------------- edge cases
@@ -222,6 +256,42 @@ def test_other_field_sizes(torch_cuda, oracle, q, schedule):
     x = W.encode(code, rng.integers(0, q, size=(4, code.K)))
     obs = W.biawgn(rng, x, code.p, 0.8)
     _lockstep(torch_cuda, oracle, code, obs, "awgn", 0.8, schedule, iters=3)
+
+
+@pytest.mark.parametrize("q", [32, 64, 128, 256])
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_lockstep_large_fields_probability_route(torch_cuda, oracle, q, schedule):
+    """The probability route for q >= 32 (shared-memory XOR-convolutions by
+    lane groups; AUTO's route up to q = 64, an explicit choice above) on
+    N = 400 symbols near the code's threshold, 8 iterations, every posterior
+    and message within 1e-5 of the oracle."""
+    from paper_cs_0605069_gb300 import workload as W
+    code = W.regular_code(q, 400, cfg=f"bigfield{q}", encodable=False)
+    rng = np.random.default_rng(q + 1)
+    F = 3
+    x = rng.integers(0, q, size=(F, code.N))
+    z = code.syndrome(x)
+    sig = W.ebn0_to_sigma(1.5)
+    obs = W.biawgn(rng, x, code.p, sig)
+    _lockstep(torch_cuda, oracle, code, obs, "awgn", sig, schedule, iters=8, syn=z.astype(np.uint8),
+              method="auto" if q <= 64 else "direct")
+
+
+@pytest.mark.parametrize("q", [128, 256])
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+def test_lockstep_large_fields_transform_route(torch_cuda, oracle, q, schedule):
+    """AUTO's route for q = 128, 256 (the transform route): held to the
+    accuracy stated for it, its largest deviation printed."""
+    from paper_cs_0605069_gb300 import workload as W
+    code = W.regular_code(q, 400, cfg=f"bigfield{q}", encodable=False)
+    rng = np.random.default_rng(q + 1)
+    x = rng.integers(0, q, size=(3, code.N))
+    z = code.syndrome(x)
+    sig = W.ebn0_to_sigma(1.5)
+    obs = W.biawgn(rng, x, code.p, sig)
+    worst = _lockstep(torch_cuda, oracle, code, obs, "awgn", sig, schedule, iters=8, syn=z.astype(np.uint8),
+                      atol=TRANSFORM_ATOL[schedule])
+    print(f"GF({q}) {schedule} transform route: worst lock-step deviation {worst:.2e}")
 
 
 @pytest.mark.parametrize("schedule", ["pus", "sus"])

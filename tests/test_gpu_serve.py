@@ -52,8 +52,11 @@ def _requests(W, n=18, seed=0):
 
 def _alone(torch, gfbp, dev_codes, r):
     cd = dev_codes[id(r["code"])]
+    # served requests run the batch kernels: for SUS with q <= 16 the level
+    # kernel folding a check's messages per visit (decode alone with FOLD)
+    kw = dict(partials="fold") if r["schedule"] == "sus" and r["code"].q <= 16 else {}
     out = gfbp.decode(cd, torch.from_numpy(r["obs"]).cuda(), r["channel"], r["param"], schedule=r["schedule"],
-                      max_iter=r["max_iter"], T=r["T"], K=r["K"])
+                      max_iter=r["max_iter"], T=r["T"], K=r["K"], **kw)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
 
@@ -83,6 +86,37 @@ def test_each_request_decodes_as_alone_while_others_run(env):
         for k in ("x_hat", "iters", "converged"):
             np.testing.assert_array_equal(res[k], ref[k], err_msg=f"q={r['code'].q} {r['schedule']} {k}")
         assert res["latency_us"] > 0 and res["rounds"] >= 1
+
+
+def test_served_requests_against_the_oracle(env, oracle):
+    """Each served request (mixed q, channels, priors, schedules, admitted while
+    others are resident) against the FP64 oracle's decode of it (Sec. 2):
+    identical decisions, counts and flags except tie and horizon frames."""
+    from tests.parity_util import classify_final, oracle_horizon
+    torch, gfbp, W = env
+    reqs = _requests(W, n=20, seed=5)
+    dev_codes = {}
+    for r in reqs:
+        if id(r["code"]) not in dev_codes:
+            dev_codes[id(r["code"])] = gfbp.Code.from_coo(r["code"])
+    srv = gfbp.Server(1 << 30, round_iters=3)
+    ids = [srv.submit(dev_codes[id(r["code"])], r["obs"], r["channel"], r["param"], T=r["T"], K=r["K"],
+                      schedule=r["schedule"], max_iter=r["max_iter"]) for r in reqs]
+    results = [srv.wait(i) for i in ids]
+    srv.close()
+    total = {"match": 0, "tie": 0, "horizon": 0, "fail": 0}
+    for r, res in zip(reqs, results):
+        kw = dict(T=r["T"], K=r["K"]) if r["T"] is not None else {}
+        ora = oracle.decode(r["code"], r["obs"], r["channel"], r["param"], r["schedule"], max_iter=r["max_iter"],
+                            trace=True, **kw)
+        hz = oracle_horizon(oracle, r["code"], r["obs"], r["channel"], r["param"], r["schedule"], r["max_iter"],
+                            **kw)
+        kinds = classify_final(res, ora, horizon=hz)
+        for k in total:
+            total[k] += int((kinds == k).sum())
+        assert not (kinds == "fail").any(), (r["code"].q, r["schedule"], r["channel"], kinds)
+    print(f"served requests against the oracle: {total}")
+    assert total["horizon"] <= 0.05 * sum(total.values()) + 1
 
 
 def test_admission_budget_timeouts_and_drain(env):
