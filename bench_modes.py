@@ -212,10 +212,11 @@ def run_serve(args):
 
 
 def run_wht(args):
-    """gfbp_wht on 2 GB of q-vectors per q in {64, 128, 256}: FP32 butterflies
-    on the CUDA cores against the FP16 hi/lo contraction on the tensor cores
-    (bytes moved: the vectors read once and written once; tensor flops: 2 q^2
-    per vector per FP16 part)."""
+    """gfbp_wht on 2 GB of q-vectors per q in {16, ..., 256}: FP32 butterflies
+    on the CUDA cores against the tensor-core form (each 16-entry chunk
+    contracted with H_16 in FP16 hi/lo parts, the chunk index transformed by
+    FP32 butterflies).  Bytes moved: the vectors read once and written once;
+    tensor flops: 2 q 16 per vector per FP16 part."""
     import torch
     from bench import ClockSampler, measured_peaks
     from paper_cs_0605069_gb300 import gfbp
@@ -224,7 +225,7 @@ def run_wht(args):
     res = {}
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    for q in (64, 128, 256):
+    for q in (16, 32, 64, 128, 256):
         n = (2 << 30) // (4 * q)
         g = torch.Generator(device="cuda").manual_seed(q)
         x = torch.rand((n, q), device="cuda", generator=g)
@@ -247,7 +248,7 @@ def run_wht(args):
             row[m] = {"ms": ms, "vectors_per_s": n / (ms / 1e3), "GB_s": gbs,
                       "frac_hbm": gbs / peaks["hbm_gbs"] if peaks else None}
             if m == "tensor":
-                tf = 2 * 2 * n * q * q / (ms / 1e3) / 1e12
+                tf = 2 * 2 * n * q * 16 / (ms / 1e3) / 1e12
                 row[m]["tensor_TFLOP_s"] = tf
         ys = gfbp.wht(x[:4096], "simt")
         yt = gfbp.wht(x[:4096], "tensor")

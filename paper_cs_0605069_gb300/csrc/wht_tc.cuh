@@ -1,12 +1,16 @@
 // Walsh-Hadamard transform of q-vectors (the convolution theorem of the
-// additive group of GF(2^p), used by the transform route of Eq. 3) as a dense
-// contraction with the +-1 Hadamard matrix on the tensor cores:
-//   Y = X H,   H[k][n] = (-1)^popcount(k AND n),
-// each FP32 operand split into an FP16 high part and an FP16 low part
-// (x = hi + lo to about 22 bits), both multiplied by H with FP32 accumulation
-// (Y = hi H + lo H).  H is exact in FP16 and is not stored: every lane builds
-// its B fragments from the indices.  Warp-level mma.sync.m16n8k16 tiles:
-// a warp task is 16 rows x 64 columns (eight 16x8 tiles) over the whole K = q.
+// additive group of GF(2^p), used by the transform route of Eq. 3) with the
+// +-1 Hadamard matrix on the tensor cores, factored as a Kronecker product:
+// with q = 16 B and index a = 16 i + l,
+//   H_q = H_B (x) H_16,   Y[i'][l'] = sum_i H_B[i'][i] sum_l x[i][l] H_16[l][l'],
+// so each 16-entry chunk of a vector is contracted with H_16 on the tensor
+// cores (Z = X H_16, K = 16: q 16 multiply-adds per vector per part instead of
+// q^2 for the dense H_q), and the B-point transforms across chunks run as FP32
+// butterflies on the contraction's accumulators (lane shuffles).  Each FP32
+// operand is split into an FP16 high part and an FP16 low part (x = hi + lo
+// to about 22 bits), both multiplied by H_16 (exact in FP16, built from index
+// parity in registers) with FP32 accumulation.  Warp-level mma.sync.m16n8k16:
+// a warp task is 16 chunks (16/B vectors) x 16 columns.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -54,59 +58,91 @@ __device__ __forceinline__ float pow2_scale(float m) {
 template <int Q>
 constexpr int tc_stride() { return Q + 8; }
 
-// out[r][c] = scale * rs[r] * sum_k (hi[r][k] + lo[r][k]) H[k][c] for rows
-// r0..r0+15 (those below nrows are written) and columns c0..c0+8*NT-1, by one
-// warp.  hi / lo: staged rows of tc_stride<Q>() halves, at least r0 + 16 rows;
-// rs: per-row factors (the inverse of the staging scale), or NULL.
-template <int Q, int NT>
-__device__ __forceinline__ void tc_wht_task(const __half* hi, const __half* lo, const float* rs, int r0, int c0,
+// out[r][:] = scale * rs[r] * WHT(hi[r][:] + lo[r][:]) for the 16/B rows of
+// task `task` (rows task*16/B ..; those below nrows are written), by one
+// warp.  The task's 16 MMA rows are the chunks (r, i) with m = (r - r_task) B
+// + i; the chunk transform over l runs on the tensor cores, the transform over
+// i (the low log2 B bits of m: MMA row bit 3 inside a thread, bits 0..2 across
+// lane bits 2..4) as FP32 butterflies on the accumulators.
+template <int Q>
+__device__ __forceinline__ void tc_wht_task(const __half* hi, const __half* lo, const float* rs, int task,
                                             float* out, int out_stride, int nrows, float scale) {
     constexpr int S = tc_stride<Q>();
+    constexpr int B = Q / 16;            // chunks per vector
+    constexpr int RT = 16 / B;           // vectors per task (B <= 16)
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    float acc[NT][4];
+    const int r0 = task * RT;
+    // the two MMA rows of this thread: m = g and m = g + 8
+    const int ma = g, mb = g + 8;
+    const int ra = r0 + ma / B, ia = ma % B, rb = r0 + mb / B, ib = mb % B;
+    float acc[2][4];
 #pragma unroll
-    for (int nt = 0; nt < NT; nt++)
+    for (int nt = 0; nt < 2; nt++)
 #pragma unroll
         for (int i = 0; i < 4; i++) acc[nt][i] = 0.f;
-#pragma unroll 4
-    for (int k0 = 0; k0 < Q; k0 += 16) {
-        const __half* ph = hi + (size_t)(r0 + g) * S + k0 + 2 * t;
-        const __half* pl = lo + (size_t)(r0 + g) * S + k0 + 2 * t;
-        const uint32_t ah[4] = {lds32(ph), lds32(ph + 8 * S), lds32(ph + 8), lds32(ph + 8 * S + 8)};
-        const uint32_t al[4] = {lds32(pl), lds32(pl + 8 * S), lds32(pl + 8), lds32(pl + 8 * S + 8)};
+    {
+        const __half* pha = hi + (size_t)ra * S + ia * 16 + 2 * t;
+        const __half* phb = hi + (size_t)rb * S + ib * 16 + 2 * t;
+        const __half* pla = lo + (size_t)ra * S + ia * 16 + 2 * t;
+        const __half* plb = lo + (size_t)rb * S + ib * 16 + 2 * t;
+        const uint32_t ah[4] = {lds32(pha), lds32(phb), lds32(pha + 8), lds32(phb + 8)};
+        const uint32_t al[4] = {lds32(pla), lds32(plb), lds32(pla + 8), lds32(plb + 8)};
 #pragma unroll
-        for (int nt = 0; nt < NT; nt++) {
-            const int n = c0 + nt * 8 + g;
-            const uint32_t b0 = had2(k0 + 2 * t, n), b1 = had2(k0 + 2 * t + 8, n);
+        for (int nt = 0; nt < 2; nt++) {
+            const int n = nt * 8 + g;
+            const uint32_t b0 = had2(2 * t, n), b1 = had2(2 * t + 8, n);
             mma16816(acc[nt], ah, b0, b1);
             mma16816(acc[nt], al, b0, b1);
         }
     }
-    const int ra = r0 + g, rb = r0 + g + 8;
+    // the B-point transforms across chunks: i = m mod B
+    if constexpr (B >= 16) {   // i bit 3: rows g and g + 8 of this thread
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const float x0 = acc[nt][c], x1 = acc[nt][2 + c];
+                acc[nt][c] = x0 + x1;
+                acc[nt][2 + c] = x0 - x1;
+            }
+    }
+#pragma unroll
+    for (int bit = 0; bit < 3; bit++) {   // i bits 0..2: g bits, lane bits 2..4
+        if ((1 << bit) < B) {
+            const int m = 4 << bit;
+            const bool up = (lane & m) != 0;
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float o = __shfl_xor_sync(0xffffffffu, acc[nt][c], m);
+                    acc[nt][c] = up ? (o - acc[nt][c]) : (acc[nt][c] + o);
+                }
+        }
+    }
     const float sa = (rs && ra < nrows) ? scale * rs[ra] : scale;
     const float sb = (rs && rb < nrows) ? scale * rs[rb] : scale;
 #pragma unroll
-    for (int nt = 0; nt < NT; nt++) {
-        const int c = c0 + nt * 8 + 2 * t;
-        if (ra < nrows) *reinterpret_cast<float2*>(out + (size_t)ra * out_stride + c) =
+    for (int nt = 0; nt < 2; nt++) {
+        const int c = nt * 8 + 2 * t;
+        if (ra < nrows) *reinterpret_cast<float2*>(out + (size_t)ra * out_stride + ia * 16 + c) =
             make_float2(acc[nt][0] * sa, acc[nt][1] * sa);
-        if (rb < nrows) *reinterpret_cast<float2*>(out + (size_t)rb * out_stride + c) =
+        if (rb < nrows) *reinterpret_cast<float2*>(out + (size_t)rb * out_stride + ib * 16 + c) =
             make_float2(acc[nt][2] * sb, acc[nt][3] * sb);
     }
 }
 
-// All rows 0..nrows-1 of a staged block by the CTA's warps (tasks of 16 rows x
-// 64 columns; q >= 16).
+// All rows 0..nrows-1 of a staged block by the CTA's warps (16 <= q <= 256).
+// The staged block must hold whole tasks: rows up to the next multiple of
+// 16/B (q / 16 = B), zero-filled beyond nrows.
 template <int Q>
 __device__ __forceinline__ void tc_wht_rows(const __half* hi, const __half* lo, const float* rs, int nrows, float* out,
                                             int out_stride, float scale, int warp, int nwarps) {
-    constexpr int NT = (Q / 8) < 8 ? (Q / 8) : 8;
-    constexpr int CB = Q / (8 * NT);   // column blocks
-    const int rblocks = (nrows + 15) / 16;
-    for (int task = warp; task < rblocks * CB; task += nwarps) {
-        const int rb = task / CB, cb = task % CB;
-        tc_wht_task<Q, NT>(hi, lo, rs, rb * 16, cb * 8 * NT, out, out_stride, nrows, scale);
-    }
+    static_assert(Q >= 16 && Q <= 256, "16 <= q <= 256");
+    constexpr int RT = 16 / (Q / 16);
+    const int tasks = (nrows + RT - 1) / RT;
+    for (int task = warp; task < tasks; task += nwarps)
+        tc_wht_task<Q>(hi, lo, rs, task, out, out_stride, nrows, scale);
 }
 
 }  // namespace

@@ -20,12 +20,13 @@ def torch_cuda():
     return torch
 
 
-def _batch(q, M=150, frames=24, f=0.02):
-    """A source that stays with probability 0.9 and noise bits flipped with
-    probability 0.02: most frames decode (at stay 0.8, f = 0.06 the code is
-    past its threshold and nearly none do)."""
+def _batch(q, M=150, frames=48, f=0.01):
+    """A source that stays with probability 0.95 and noise bits flipped with
+    probability 0.01: nearly every frame decodes (the horizon class is for
+    frames that do not; at stay 0.8, f = 0.06 the code is past its threshold
+    and nearly none decode)."""
     from paper_cs_0605069_gb300 import workload as W
-    return W.mn_batch(q, M, frames, f, stay=0.9, cfg=f"mn_test_{q}")
+    return W.mn_batch(q, M, frames, f, stay=0.95, cfg=f"mn_test_{q}")
 
 
 def test_mn_syndromes_are_those_of_the_received_word():
@@ -41,7 +42,7 @@ def test_mn_syndromes_are_those_of_the_received_word():
 def test_mn_lockstep(torch_cuda, oracle, q, schedule):
     import torch
     from paper_cs_0605069_gb300 import gfbp
-    b = _batch(q, frames=6)
+    b = _batch(q, frames=6, f=0.02)
     cd = gfbp.Code.from_coo(b.code)
     F = b.obs.shape[0]
     msg = oracle.initial_messages(b.code, b.obs, "bsc", b.f, T=b.T, K=b.K, punct=b.punct)
