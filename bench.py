@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--layout", default="auto", choices=["auto", "lanes", "thread", "resident", "l2resident"])
     ap.add_argument("--partials", default="auto", choices=["auto", "fold", "running", "running_global"],
                     help="SUS level kernel: check messages folded per visit or carried as running partials")
-    ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve", "wht", "paper", "fig1"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "mixed", "serve", "wht", "markov", "paper", "fig1"],
                     help="batch: the GF(16) N=1000 benchmark (default); mixed: frames of 12 (q, N) classes in one "
                          "persistent launch; serve: Poisson arrivals to the continuous-batching server")
     ap.add_argument("--duration", type=float, default=6.0, help="serve: seconds per offered load")
@@ -340,6 +340,10 @@ def main():
     if args.workload == "wht":
         from bench_modes import run_wht
         run_wht(args)
+        return
+    if args.workload == "markov":
+        from bench_modes import run_markov
+        run_markov(args)
         return
     if args.workload == "paper":
         from bench_modes import run_paper

@@ -211,6 +211,94 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_markov(args):
+    """The Markov-source configuration: GF(8), regular (3,6), N = 2000, a
+    stationary chain with self-transition 0.8, BSC 0.08 / 0.10 (round-robin
+    over frames) and BEC 0.40, 2048 frames each, PUS and SUS, max 200
+    iterations, the dynamical block priors (Eqs. 6-7) on; the same frames
+    decoded with the i.i.d. prior give the gain of the source model.  Each
+    decode is timed alone (CUDA events around the schedule kernel, L2 flushed
+    before it); symbol-iterations/s and the HBM model (PUS 52q, SUS 28q bytes
+    per symbol-iteration; the block priors add 2q per source symbol and
+    iteration, not counted) as in the main benchmark."""
+    import torch
+    from bench import ALG_BYTES_PER_SYMITER, measured_peaks
+    from paper_cs_0605069_gb300 import gfbp, workload as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clocks = _clock_sampler()
+    clocks.start()
+    res = {}
+    F = args.frames if args.frames != 4096 else 2048
+    for name in ("gf8_n2000_markov_bsc", "gf8_n2000_markov_bec"):
+        b = W.make_batch(name, frames=F)
+        code = gfbp.Code.from_coo(b.code)
+        N, q = b.code.N, b.code.q
+        obs = torch.from_numpy(b.obs).to(dev)
+        fp = torch.from_numpy(b.param.astype(np.float32)).to(dev)
+        levels = sorted(set(float(v) for v in b.param))
+        row = {}
+        for prior in ("markov", "iid"):
+            pk = dict(T=b.T, K=b.K) if prior == "markov" else {}
+            for sched in ("pus", "sus"):
+                ws = torch.empty(gfbp.workspace_size(code, F, sched, pk.get("T"), pk.get("K", 0)), dtype=torch.uint8,
+                                 device=dev)
+                out = dict(x_hat=torch.empty((F, N), dtype=torch.uint8, device=dev),
+                           iters=torch.empty(F, dtype=torch.int32, device=dev),
+                           converged=torch.empty(F, dtype=torch.uint8, device=dev))
+
+                def run(ev=None):
+                    gfbp.decode(code, obs, b.channel, 0.0, schedule=sched, max_iter=b.max_iter, frame_param=fp,
+                                workspace=ws, out=out, kernel_events=ev, **pk)
+
+                for _ in range(max(args.warmup, 3)):
+                    flush.fill_(1.0)
+                    run()
+                ms = []
+                for _ in range(args.steps):
+                    flush.fill_(1.0)
+                    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                    run(ev)
+                    torch.cuda.synchronize()
+                    ms.append(ev[0].elapsed_time(ev[1]))
+                kms = float(np.mean(ms))
+                it = out["iters"].cpu().numpy()
+                conv = out["converged"].cpu().numpy().astype(bool)
+                xh = out["x_hat"].cpu().numpy()
+                symit = float(it.sum()) * N
+                gbs = ALG_BYTES_PER_SYMITER[sched] * q * symit / (kms / 1e3) / 1e9
+                by = {}
+                for lv in levels:
+                    sel = b.param.astype(np.float64) == lv
+                    by[str(lv)] = {"ser": float((xh[sel] != b.x[sel]).mean()),
+                                   "fer": float((xh[sel] != b.x[sel]).any(1).mean()),
+                                   "converged": float(conv[sel].mean()), "mean_iters": float(it[sel].mean())}
+                row[f"{sched}_{prior}"] = {"kernel_ms": kms, "frames_per_s": F / (kms / 1e3),
+                                           "sym_iter_per_s": symit / (kms / 1e3), "mean_iters": float(it.mean()),
+                                           "converged": float(conv.mean()), "hbm_model_GB_s": gbs,
+                                           "hbm_model_frac": gbs / hbm_peak, "by_param": by}
+        for sched in ("pus", "sus"):
+            m, i = row[f"{sched}_markov"], row[f"{sched}_iid"]
+            row[f"{sched}_gain"] = {"iters_iid_over_markov": i["mean_iters"] / m["mean_iters"],
+                                    "converged_markov_minus_iid": m["converged"] - i["converged"]}
+        row["sus_pus_iteration_ratio"] = row["sus_markov"]["mean_iters"] / row["pus_markov"]["mean_iters"]
+        res[name] = row
+    cl = clocks.stop()
+    total_frames = 2 * 2 * F   # both channels, both schedules, Markov prior
+    total_ms = sum(res[n][f"{s}_markov"]["kernel_ms"] for n in res for s in ("pus", "sus"))
+    line = {"metric": "decoded frames/s, Markov source with dynamical block priors, SUS and PUS", "workload": "markov",
+            "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "value": total_frames / (total_ms / 1e3), "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (seeded Markov sources, systematic encoding)",
+            "config": {"q": 8, "N": 2000, "code": "regular (3,6) rate 1/2", "frames": F, "max_iter": 200,
+                       "source": "stationary chain, self-transition 0.8", "l2": "flushed before every decode"},
+            "per_workload": res, "clocks": cl}
+    print(json.dumps(line))
+
+
 def run_wht(args):
     """gfbp_wht on 2 GB of q-vectors per q in {16, ..., 256}: FP32 butterflies
     on the CUDA cores against the tensor-core form (each 16-entry chunk

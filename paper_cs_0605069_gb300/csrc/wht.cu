@@ -27,61 +27,101 @@ __global__ void __launch_bounds__(256) k_wht_simt(const float* __restrict__ x, f
     }
 }
 
-constexpr int kTcRows = 64;   // rows staged per block step
-
+// The streaming tensor-core transform: a warp task is 16 chunks of 16 entries
+// (16 / B vectors, B = q / 16 chunks each); MMA row m of a task is chunk m % B
+// of vector task * 16 / B + m / B.  Every lane reads its eight entries of the
+// A fragments straight from global memory (rows g and g + 8, columns 2t, 2t+1,
+// 2t+8, 2t+9 of the chunk: 32 contiguous bytes per chunk and instruction
+// across the four lanes of a row), splits them into FP16 parts in registers
+// and writes its outputs at the same positions; the next task's entries are
+// loaded before the current one is transformed.
 template <int Q>
-constexpr size_t tc_smem() {
-    return sizeof(__half) * 2 * (size_t)kTcRows * tc_stride<Q>() + sizeof(float) * kTcRows;
+__device__ __forceinline__ void tc_load(const float* __restrict__ x, long long n, long long task, float (&v)[8]) {
+    constexpr int B = Q / 16, RT = 16 / B;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const long long ra = task * RT + g / B, rb = task * RT + (g + 8) / B;
+    const int ia = g % B, ib = (g + 8) % B;
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+    if (ra < n) {
+        const float2* p = reinterpret_cast<const float2*>(x + (size_t)ra * Q + ia * 16 + 2 * t);
+        a0 = __ldcs(p);
+        a1 = __ldcs(p + 4);
+    }
+    if (rb < n) {
+        const float2* p = reinterpret_cast<const float2*>(x + (size_t)rb * Q + ib * 16 + 2 * t);
+        b0 = __ldcs(p);
+        b1 = __ldcs(p + 4);
+    }
+    v[0] = a0.x; v[1] = a0.y; v[2] = a1.x; v[3] = a1.y;
+    v[4] = b0.x; v[5] = b0.y; v[6] = b1.x; v[7] = b1.y;
 }
 
-// One warp stages a row: its largest magnitude, the power-of-two scale, the
-// FP16 parts of the scaled entries; rs[r] receives the inverse scale.
+__device__ __forceinline__ uint32_t pack_half2(__half lo_index, __half hi_index) {
+    return (uint32_t)__half_as_ushort(lo_index) | ((uint32_t)__half_as_ushort(hi_index) << 16);
+}
+
 template <int Q>
-__device__ __forceinline__ void stage_row(const float* src, bool valid, __half* hi, __half* lo, float* rs, int lane) {
-    constexpr int PER = (Q + 127) / 128;   // float4 chunks per lane
-    float4 v[PER];
-    float m = 0.f;
+__device__ __forceinline__ void tc_transform_store(float* __restrict__ y, long long n, long long task, const float (&v)[8]) {
+    constexpr int B = Q / 16, RT = 16 / B;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // largest magnitude of the vector of each of the two rows, over the lanes
+    // that hold its chunks (t bits and the g bits below log2 B)
+    float ma = fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3])));
+    float mb = fmaxf(fmaxf(fabsf(v[4]), fabsf(v[5])), fmaxf(fabsf(v[6]), fabsf(v[7])));
+    if constexpr (B == 16) ma = mb = fmaxf(ma, mb);   // rows g and g + 8: one vector
 #pragma unroll
-    for (int i = 0; i < PER; i++) {
-        const int k = (i * 32 + lane) * 4;
-        v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid && k < Q) v[i] = *reinterpret_cast<const float4*>(src + k);
-        m = fmaxf(m, fmaxf(fmaxf(fabsf(v[i].x), fabsf(v[i].y)), fmaxf(fabsf(v[i].z), fabsf(v[i].w))));
+    for (int m = 1; m <= 2; m <<= 1) {
+        ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, m));
+        mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, m));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const float s = pow2_scale(m);
-#pragma unroll
-    for (int i = 0; i < PER; i++) {
-        const int k = (i * 32 + lane) * 4;
-        if (k < Q) {
-            __half h[4], l[4];
-            split_hilo(v[i].x * s, h[0], l[0]);
-            split_hilo(v[i].y * s, h[1], l[1]);
-            split_hilo(v[i].z * s, h[2], l[2]);
-            split_hilo(v[i].w * s, h[3], l[3]);
-            *reinterpret_cast<uint2*>(hi + k) = *reinterpret_cast<const uint2*>(h);
-            *reinterpret_cast<uint2*>(lo + k) = *reinterpret_cast<const uint2*>(l);
+    for (int bit = 0; bit < 3; bit++) {
+        if ((1 << bit) < B) {
+            ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, 4 << bit));
+            mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, 4 << bit));
         }
     }
-    if (lane == 0) *rs = 1.0f / s;
+    const float sa = pow2_scale(ma), sb = pow2_scale(mb);
+    __half h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) split_hilo(v[i] * (i < 4 ? sa : sb), h[i], l[i]);
+    const uint32_t ah[4] = {pack_half2(h[0], h[1]), pack_half2(h[4], h[5]), pack_half2(h[2], h[3]),
+                            pack_half2(h[6], h[7])};
+    const uint32_t al[4] = {pack_half2(l[0], l[1]), pack_half2(l[4], l[5]), pack_half2(l[2], l[3]),
+                            pack_half2(l[6], l[7])};
+    float acc[2][4];
+    tc_wht_frag<Q>(ah, al, acc);
+    const long long ra = task * RT + g / B, rb = task * RT + (g + 8) / B;
+    const int ia = g % B, ib = (g + 8) % B;
+    const float ua = 1.0f / sa, ub = 1.0f / sb;   // powers of two: exact
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++) {
+        const int c = nt * 8 + 2 * t;
+        if (ra < n) __stcs(reinterpret_cast<float2*>(y + (size_t)ra * Q + ia * 16 + c),
+                           make_float2(acc[nt][0] * ua, acc[nt][1] * ua));
+        if (rb < n) __stcs(reinterpret_cast<float2*>(y + (size_t)rb * Q + ib * 16 + c),
+                           make_float2(acc[nt][2] * ub, acc[nt][3] * ub));
+    }
 }
 
 template <int Q>
-__global__ void __launch_bounds__(256) k_wht_tc(const float* x, float* y, long long n) {
-    constexpr int S = tc_stride<Q>();
-    extern __shared__ __align__(16) __half s_stage[];
-    __half* hi = s_stage;
-    __half* lo = s_stage + (size_t)kTcRows * S;
-    float* rs = reinterpret_cast<float*>(s_stage + (size_t)2 * kTcRows * S);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-    for (long long base = (long long)blockIdx.x * kTcRows; base < n; base += (long long)gridDim.x * kTcRows) {
-        const int nrows = (int)((n - base) < kTcRows ? (n - base) : kTcRows);
-        for (int r = warp; r < kTcRows; r += nw)
-            stage_row<Q>(x + (size_t)(base + r) * Q, r < nrows, hi + (size_t)r * S, lo + (size_t)r * S, rs + r, lane);
-        __syncthreads();
-        tc_wht_rows<Q>(hi, lo, rs, nrows, y + (size_t)base * Q, Q, 1.0f, warp, nw);
-        __syncthreads();
+__global__ void __launch_bounds__(256) k_wht_tc(const float* __restrict__ x, float* __restrict__ y, long long n) {
+    constexpr int RT = 16 / (Q / 16);
+    const long long tasks = (n + RT - 1) / RT;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    long long task = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);   // warp-uniform
+    if (task >= tasks) return;
+    float cur[8];
+    tc_load<Q>(x, n, task, cur);
+    for (; task < tasks; task += nw) {
+        const bool more = task + nw < tasks;
+        float nxt[8];
+        if (more) tc_load<Q>(x, n, task + nw, nxt);
+        tc_transform_store<Q>(y, n, task, cur);
+        if (more) {
+#pragma unroll
+            for (int i = 0; i < 8; i++) cur[i] = nxt[i];
+        }
     }
 }
 
@@ -97,16 +137,17 @@ cudaError_t launch_wht(const float* x, float* y, long long n, int method, cudaSt
         return cudaGetLastError();
     }
     if constexpr (Q >= 16) {
-        constexpr size_t smem = tc_smem<Q>();
         int occ = 0;
-        cudaError_t e = kernel_prepare((const void*)k_wht_tc<Q>, 256, smem, &occ);
+        cudaError_t e = kernel_prepare((const void*)k_wht_tc<Q>, 256, 0, &occ);
         if (e != cudaSuccess) return e;
         if (occ < 1) occ = 1;
-        long long blocks = (n + kTcRows - 1) / kTcRows;
+        constexpr int RT = 16 / (Q / 16);
+        const long long tasks = (n + RT - 1) / RT;
+        long long blocks = (tasks + 7) / 8;
         const long long cap = (long long)sm_count() * occ;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) return cudaSuccess;
-        k_wht_tc<Q><<<(int)blocks, 256, smem, s>>>(x, y, n);
+        k_wht_tc<Q><<<(int)blocks, 256, 0, s>>>(x, y, n);
         return cudaGetLastError();
     }
     return cudaErrorInvalidValue;

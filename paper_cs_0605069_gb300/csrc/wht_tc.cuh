@@ -58,44 +58,27 @@ __device__ __forceinline__ float pow2_scale(float m) {
 template <int Q>
 constexpr int tc_stride() { return Q + 8; }
 
-// out[r][:] = scale * rs[r] * WHT(hi[r][:] + lo[r][:]) for the 16/B rows of
-// task `task` (rows task*16/B ..; those below nrows are written), by one
-// warp.  The task's 16 MMA rows are the chunks (r, i) with m = (r - r_task) B
-// + i; the chunk transform over l runs on the tensor cores, the transform over
-// i (the low log2 B bits of m: MMA row bit 3 inside a thread, bits 0..2 across
-// lane bits 2..4) as FP32 butterflies on the accumulators.
+// The transform of one warp task from its A fragments (the FP16 high and low
+// parts of the 16 chunks x 16 entries, in the m16n8k16 row-major layout:
+// a[0] row g cols 2t..2t+1, a[1] row g+8, a[2] row g cols 2t+8.., a[3] row
+// g+8 cols 2t+8..).  MMA row m is chunk i = m mod B of vector m / B.  The
+// chunk transform over l runs on the tensor cores; the transform over i (the
+// low log2 B bits of m: row bit 3 inside a thread, bits 0..2 across lane bits
+// 2..4) as FP32 butterflies on the accumulators.  acc[nt][0..1]: row g,
+// columns nt*8 + 2t, +1; acc[nt][2..3]: row g + 8.
 template <int Q>
-__device__ __forceinline__ void tc_wht_task(const __half* hi, const __half* lo, const float* rs, int task,
-                                            float* out, int out_stride, int nrows, float scale) {
-    constexpr int S = tc_stride<Q>();
-    constexpr int B = Q / 16;            // chunks per vector
-    constexpr int RT = 16 / B;           // vectors per task (B <= 16)
+__device__ __forceinline__ void tc_wht_frag(const uint32_t (&ah)[4], const uint32_t (&al)[4], float (&acc)[2][4]) {
+    constexpr int B = Q / 16;
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int r0 = task * RT;
-    // the two MMA rows of this thread: m = g and m = g + 8
-    const int ma = g, mb = g + 8;
-    const int ra = r0 + ma / B, ia = ma % B, rb = r0 + mb / B, ib = mb % B;
-    float acc[2][4];
 #pragma unroll
-    for (int nt = 0; nt < 2; nt++)
+    for (int nt = 0; nt < 2; nt++) {
 #pragma unroll
         for (int i = 0; i < 4; i++) acc[nt][i] = 0.f;
-    {
-        const __half* pha = hi + (size_t)ra * S + ia * 16 + 2 * t;
-        const __half* phb = hi + (size_t)rb * S + ib * 16 + 2 * t;
-        const __half* pla = lo + (size_t)ra * S + ia * 16 + 2 * t;
-        const __half* plb = lo + (size_t)rb * S + ib * 16 + 2 * t;
-        const uint32_t ah[4] = {lds32(pha), lds32(phb), lds32(pha + 8), lds32(phb + 8)};
-        const uint32_t al[4] = {lds32(pla), lds32(plb), lds32(pla + 8), lds32(plb + 8)};
-#pragma unroll
-        for (int nt = 0; nt < 2; nt++) {
-            const int n = nt * 8 + g;
-            const uint32_t b0 = had2(2 * t, n), b1 = had2(2 * t + 8, n);
-            mma16816(acc[nt], ah, b0, b1);
-            mma16816(acc[nt], al, b0, b1);
-        }
+        const int n = nt * 8 + g;
+        const uint32_t b0 = had2(2 * t, n), b1 = had2(2 * t + 8, n);
+        mma16816(acc[nt], ah, b0, b1);
+        mma16816(acc[nt], al, b0, b1);
     }
-    // the B-point transforms across chunks: i = m mod B
     if constexpr (B >= 16) {   // i bit 3: rows g and g + 8 of this thread
 #pragma unroll
         for (int nt = 0; nt < 2; nt++)
@@ -120,6 +103,30 @@ __device__ __forceinline__ void tc_wht_task(const __half* hi, const __half* lo, 
                 }
         }
     }
+}
+
+// out[r][:] = scale * rs[r] * WHT(hi[r][:] + lo[r][:]) for the 16/B rows of
+// task `task` (rows task*16/B ..; those below nrows are written), by one
+// warp, from staged FP16 parts (rows of tc_stride<Q>() halves).
+template <int Q>
+__device__ __forceinline__ void tc_wht_task(const __half* hi, const __half* lo, const float* rs, int task,
+                                            float* out, int out_stride, int nrows, float scale) {
+    constexpr int S = tc_stride<Q>();
+    constexpr int B = Q / 16;            // chunks per vector
+    constexpr int RT = 16 / B;           // vectors per task (B <= 16)
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int r0 = task * RT;
+    // the two MMA rows of this thread: m = g and m = g + 8
+    const int ma = g, mb = g + 8;
+    const int ra = r0 + ma / B, ia = ma % B, rb = r0 + mb / B, ib = mb % B;
+    const __half* pha = hi + (size_t)ra * S + ia * 16 + 2 * t;
+    const __half* phb = hi + (size_t)rb * S + ib * 16 + 2 * t;
+    const __half* pla = lo + (size_t)ra * S + ia * 16 + 2 * t;
+    const __half* plb = lo + (size_t)rb * S + ib * 16 + 2 * t;
+    const uint32_t ah[4] = {lds32(pha), lds32(phb), lds32(pha + 8), lds32(phb + 8)};
+    const uint32_t al[4] = {lds32(pla), lds32(plb), lds32(pla + 8), lds32(plb + 8)};
+    float acc[2][4];
+    tc_wht_frag<Q>(ah, al, acc);
     const float sa = (rs && ra < nrows) ? scale * rs[ra] : scale;
     const float sb = (rs && rb < nrows) ? scale * rs[rb] : scale;
 #pragma unroll
