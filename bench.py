@@ -72,6 +72,8 @@ def parse():
                          "persistent launch; serve: Poisson arrivals to the continuous-batching server")
     ap.add_argument("--duration", type=float, default=6.0, help="serve: seconds per offered load")
     ap.add_argument("--noise-scale", type=float, default=1.0, help="paper: multiplier of Table 1's noise levels")
+    ap.add_argument("--wht-q", type=int, default=0, help="wht: one field size only (profiling cases)")
+    ap.add_argument("--wht-mb", type=int, default=2048, help="wht: MiB of input vectors per field size")
     return ap.parse_args()
 
 

@@ -279,6 +279,14 @@ typedef struct {
                                 so results are the same bit for bit. */
     int32_t layout;          /* gfbp_layout */
     int32_t sus_partials;    /* gfbp_sus_partials */
+    int32_t* zero_sums;      /* device [F] or NULL: per frame, the number of message and
+                                posterior normalisations (r_ij by Eq. 3, q_ij by Eq. 4, Q_j
+                                by Eq. 5) whose sum was zero or not finite and that fell
+                                back to the uniform vector, set by this call (a device-side
+                                anomaly status word: decoding goes on, nothing traps).  A
+                                zero sum arises where the evidence contradicts itself, e.g.
+                                a symbol observed without erasure against a syndrome that
+                                excludes it. */
 } gfbp_options;
 
 /*
@@ -357,16 +365,32 @@ gfbp_status gfbp_step(const gfbp_code* code, int32_t n_frames, const float* obs,
  * it twice and divide by q for the identity).  x, y: device [n][q] float32,
  * 16-byte aligned; y may equal x.
  *   GFBP_WHT_SIMT    FP32 butterflies on the CUDA cores (any q).
- *   GFBP_WHT_TENSOR  dense +-1 contraction on the tensor cores: each x split
- *                    into FP16 high and low parts (|x| < 65504), FP32
- *                    accumulation; q in {16, ..., 256}.  Each vector is
- *                    scaled by a power of two to a largest |x| in [1, 2)
- *                    first (undone exactly).  Error per output below
+ *   GFBP_WHT_TENSOR  the +-1 Hadamard matrix as H_{q/16} (x) H_16: every
+ *                    16-entry chunk contracted with H_16 on the tensor cores
+ *                    (each x split into FP16 high and low parts, FP32
+ *                    accumulation), then FP32 butterflies across the q/16
+ *                    chunks; q in {16, ..., 256}.  Each vector is scaled by
+ *                    a power of two to a largest |x| in [1, 2) first (undone
+ *                    exactly).  Error per output below
  *                    2^-19 sum_a |x[a]| + q 2^-24 max_a |x[a]| (tested).
  * Enqueued on `stream`.
  */
 typedef enum { GFBP_WHT_SIMT = 0, GFBP_WHT_TENSOR = 1 } gfbp_wht_method;
 gfbp_status gfbp_wht(const float* x, float* y, int64_t n, int32_t q, int32_t method, void* stream);
+
+/*
+ * Self-test of the decoder kernels' bounded device waits: runs one of them on
+ * a condition that never comes true, on `stream`, and waits for it.
+ *   which 0: the mbarrier wait of the bulk copies (an mbarrier that expects
+ *            one arrival; none is made).
+ *   which 1: the watermark wait of the multi-team SUS kernel (a progress word
+ *            that never passes the awaited column).
+ *   completed  host: 1 if the wait completed, 0 if it ran out.
+ * Returns GFBP_ETIMEOUT when the wait ran out, which is the expected outcome
+ * (the kernel returns normally and the context stays usable); GFBP_OK would
+ * mean the wait completed without its condition.  Takes up to about a second.
+ */
+gfbp_status gfbp_wait_selftest(int32_t which, int32_t* completed, void* stream);
 
 /* --------------------------------------------------------------- batching */
 /*
@@ -473,7 +497,10 @@ typedef struct {
     size_t bytes_in_use, peak_bytes;
 } gfbp_server_stats_t;
 
-/* round_iters >= 1: iterations a resident frame advances per round. */
+/* round_iters >= 1: iterations a resident frame advances per round at most;
+ * frames whose iteration costs more than a GF(16), N = 1000 frame's advance
+ * proportionally fewer (at least one), so that a round is not held by the
+ * costliest request for round_iters of its iterations. */
 gfbp_status gfbp_server_create(size_t hbm_budget_bytes, int32_t round_iters, gfbp_server** out);
 /* Queue a request (thread-safe).  GFBP_EINVAL if its footprint exceeds the
  * whole budget; GFBP_EBUSY while the server drains.  The output buffers must

@@ -263,9 +263,13 @@ __global__ void __launch_bounds__(kMixedThreads) k_sus_mixed(const DecodeArgs* _
     }
 }
 
-// SUS, CTA family: one frame per CTA (level schedules).
+// SUS, CTA family: one frame per CTA (level schedules).  With 256 threads
+// (a lane-group variant present) three CTAs per SM, as the transform- and
+// probability-route level kernels of q >= 32 reach on their own (80
+// registers): those items hold most of a mixed batch's work, and two CTAs per
+// SM (128 registers) left a third of their slots empty.
 template <int NTH>
-__global__ void __launch_bounds__(NTH, 512 / NTH) k_sus_mixed_cta(const DecodeArgs* __restrict__ items,
+__global__ void __launch_bounds__(NTH, NTH == 256 ? 3 : 4) k_sus_mixed_cta(const DecodeArgs* __restrict__ items,
                                                                     const int* __restrict__ prefix,
                                                                     const int* __restrict__ variant, int n_items,
                                                                     int total, int* counter, const int* field_item) {

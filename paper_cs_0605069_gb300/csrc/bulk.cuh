@@ -51,11 +51,21 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
     if (bytes) bulk_copy(dst, src, bytes, bar);
 }
 
-constexpr int kBulkWaitLimit = 1 << 24;   // polls before a wait gives up
+// A wait gives up after about a second (the global nanosecond timer; a poll
+// may suspend the thread for microseconds), or after kBulkWaitLimit polls.
+constexpr unsigned long long kBulkWaitNs = 1000000000ull;
+constexpr int kBulkWaitLimit = 1 << 24;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Wait for the completion of the phase with the given parity; false when the
 // bound ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
     for (int n = 0; n < kBulkWaitLimit; n++) {
         uint32_t done;
         asm volatile(
@@ -64,6 +74,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(smem_addr(bar)), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((n & 63) == 63 && global_ns() - t0 > kBulkWaitNs) return false;
     }
     return false;
 }

@@ -283,6 +283,7 @@ gfbp_status fill_args(DecodeArgs& A, const gfbp_code* code, int32_t F, const flo
     A.step = step;
     A.msg_io = msg_io;
     A.prior_out = prior_out;
+    A.zsum = opt ? opt->zero_sums : nullptr;
     const int m = opt ? opt->check_method : GFBP_CHECK_AUTO;
     if (m < GFBP_CHECK_AUTO || m > GFBP_CHECK_TENSOR) {
         set_error("unknown check_method");
@@ -404,6 +405,7 @@ gfbp_status run(const gfbp_code* code, int32_t F, const float* obs, gfbp_channel
         }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(A.work, 0, sizeof(int), stream);
+    if (e == cudaSuccess && A.zsum) e = cudaMemsetAsync(A.zsum, 0, sizeof(int) * (size_t)F, stream);
     if (e == cudaSuccess) e = launch_channel(A, stream);
     // (the resident kernels initialise their messages in shared memory)
     if (e == cudaSuccess && schedule == GFBP_SUS && !resident) e = launch_init_dev(A, stream);

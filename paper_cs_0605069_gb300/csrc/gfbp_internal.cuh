@@ -108,7 +108,20 @@ struct DecodeArgs {
     // convolution of the sweep-start messages of positions m..d-1 and slot e0
     // the prefix of the messages updated so far
     float* sfx;
+    // per frame the normalisations (of r, q and Q) whose sum was zero or not
+    // finite and that fell back to the uniform vector, or NULL
+    int* zsum;
 };
+
+// The frame's zero-sum counter, or NULL when it is not asked for.
+__device__ __forceinline__ int* zsum_of(const DecodeArgs& A, int f) { return A.zsum ? A.zsum + f : nullptr; }
+
+// Count one uniform fallback; a lane group of G lanes (aligned in the warp)
+// counts it once.
+template <int G>
+__device__ __forceinline__ void note_zero_sum(int* zs) {
+    if (zs && (threadIdx.x & (G - 1)) == 0) atomicAdd(zs, 1);
+}
 
 // ---------------------------------------------------------------- helpers
 template <int G>
@@ -198,17 +211,21 @@ __device__ __forceinline__ void wht(float (&x)[Lay<Q>::V], unsigned mask, int g)
 template <int Q>
 __device__ __forceinline__ float gsum(const float (&x)[Lay<Q>::V], unsigned mask) {
     constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
+    // (separately rounded additions throughout, here and in every sum that
+    // normalises a message: a product feeding the sum is never fused into it,
+    // so every kernel forms the same sums)
     float s = 0.f;
 #pragma unroll
-    for (int i = 0; i < V; i++) s += x[i];
+    for (int i = 0; i < V; i++) s = __fadd_rn(s, x[i]);
 #pragma unroll
-    for (int m = 1; m < G; m <<= 1) s += __shfl_xor_sync(mask, s, m);
+    for (int m = 1; m < G; m <<= 1) s = __fadd_rn(s, __shfl_xor_sync(mask, s, m));
     return s;
 }
 
-// Scale to sum 1; a zero or non-finite sum gives the uniform vector.
+// Scale to sum 1; a zero or non-finite sum gives the uniform vector (counted
+// in *zs when zs is not NULL).
 template <int Q>
-__device__ __forceinline__ void gnormalise(float (&x)[Lay<Q>::V], unsigned mask) {
+__device__ __forceinline__ void gnormalise(float (&x)[Lay<Q>::V], unsigned mask, int* zs = nullptr) {
     constexpr int V = Lay<Q>::V;
     const float s = gsum<Q>(x, mask);
     if (s > 0.f && s <= 3.0e38f) {
@@ -218,6 +235,7 @@ __device__ __forceinline__ void gnormalise(float (&x)[Lay<Q>::V], unsigned mask)
     } else {
 #pragma unroll
         for (int i = 0; i < V; i++) x[i] = 1.0f / Q;
+        note_zero_sum<Lay<Q>::G>(zs);
     }
 }
 
@@ -322,7 +340,7 @@ __device__ __forceinline__ void wht_n(float (&x)[NB][Lay<Q>::V], unsigned mask, 
 template <int Q, int NB>
 __device__ __forceinline__ void dev_finish_n(float (&x)[NB][Lay<Q>::V], const int (&C)[NB], const int (&h)[NB],
                                              const int (&z)[NB], int n, float* sc, unsigned mask, int g,
-                                             const uint8_t* ex, const uint8_t* lg) {
+                                             const uint8_t* ex, const uint8_t* lg, int* zs = nullptr) {
     constexpr int V = Lay<Q>::V;
     wht_n<Q, NB>(x, mask, g);
 #pragma unroll
@@ -347,7 +365,7 @@ __device__ __forceinline__ void dev_finish_n(float (&x)[NB][Lay<Q>::V], const in
     __syncwarp(mask);
 #pragma unroll
     for (int k = 0; k < NB; k++)
-        if (k < n) gnormalise<Q>(x[k], mask);
+        if (k < n) gnormalise<Q>(x[k], mask, zs);
 }
 
 // Vertical-pass epilogue for NB normalised messages q (n in use): the stored
@@ -439,13 +457,13 @@ __device__ __forceinline__ void to_deviation(float (&x)[Lay<Q>::V], int h, float
 
 template <int Q>
 __device__ __forceinline__ void dev_finish(float (&x)[Lay<Q>::V], int C, int h, int z, float* sc, unsigned mask,
-                                           int g, const uint8_t* ex, const uint8_t* lg) {
+                                           int g, const uint8_t* ex, const uint8_t* lg, int* zs = nullptr) {
     constexpr int V = Lay<Q>::V;
     float xx[1][V];
     const int cc[1] = {C}, hh[1] = {h}, zz[1] = {z};
 #pragma unroll
     for (int v = 0; v < V; v++) xx[0][v] = x[v];
-    dev_finish_n<Q, 1>(xx, cc, hh, zz, 1, sc, mask, g, ex, lg);
+    dev_finish_n<Q, 1>(xx, cc, hh, zz, 1, sc, mask, g, ex, lg, zs);
 #pragma unroll
     for (int v = 0; v < V; v++) x[v] = xx[0][v];
 }
@@ -543,7 +561,7 @@ __device__ __forceinline__ void xconv_sm2(float (&out1)[Lay<Q>::V], float (&out2
 template <int Q, int NB>
 __device__ __forceinline__ void direct_finish_n(float (&x)[NB][Lay<Q>::V], const int (&h)[NB], const int (&z)[NB],
                                                 int n, float* sc, unsigned mask, int g, const uint8_t* ex,
-                                                const uint8_t* lg) {
+                                                const uint8_t* lg, int* zs = nullptr) {
     constexpr int V = Lay<Q>::V;
 #pragma unroll
     for (int k = 0; k < NB; k++)
@@ -559,7 +577,7 @@ __device__ __forceinline__ void direct_finish_n(float (&x)[NB][Lay<Q>::V], const
     __syncwarp(mask);
 #pragma unroll
     for (int k = 0; k < NB; k++)
-        if (k < n) gnormalise<Q>(x[k], mask);
+        if (k < n) gnormalise<Q>(x[k], mask, zs);
 }
 
 // p_j: normalised channel likelihood times the block prior of a source symbol.

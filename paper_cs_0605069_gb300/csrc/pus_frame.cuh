@@ -65,7 +65,7 @@ __device__ __forceinline__ void pus_check(const DecodeArgs& A, float* slab, int 
             const int C = __shfl_sync(mask, cpre ^ Cs[k], lane0);
             dev_combine<V>(pre, D);
             cpre ^= c;
-            dev_finish<Q>(x, C, A.c.eh[e0 + k], z, sc, mask, g, ex, lg);
+            dev_finish<Q>(x, C, A.c.eh[e0 + k], z, sc, mask, g, ex, lg, zsum_of(A, f));
             stv<V>(slab + (size_t)(e0 + k) * Q + g * V, x);
         }
     }
@@ -134,7 +134,7 @@ __device__ __forceinline__ void pus_check_direct(const DecodeArgs& A, float* sla
                 __syncwarp(mask);
             }
             const int hh[1] = {A.c.eh[e0 + k]}, zz[1] = {z};
-            direct_finish_n<Q, 1>(out, hh, zz, 1, T1, mask, g, ex, lg);
+            direct_finish_n<Q, 1>(out, hh, zz, 1, T1, mask, g, ex, lg, zsum_of(A, f));
             stv<V>(slab + (size_t)(e0 + k) * Q + g * V, out[0]);
         }
     }
@@ -169,7 +169,7 @@ __device__ __forceinline__ void pus_var(const DecodeArgs& A, float* slab, int f,
         float Qj[V];
 #pragma unroll
         for (int v = 0; v < V; v++) Qj[v] = p[v] * acc[v];
-        gnormalise<Q>(Qj, mask);
+        gnormalise<Q>(Qj, mask, zsum_of(A, f));
         const int a = gargmax<Q>(Qj, mask, g);
         if (g == 0) A.xhat[(size_t)f * A.c.N + j] = (uint8_t)a;
         if (A.post) stv<V>(A.post + ((size_t)f * A.c.N + j) * Q + g * V, Qj);
@@ -192,7 +192,7 @@ __device__ __forceinline__ void pus_var(const DecodeArgs& A, float* slab, int f,
                 x[v] = p[v] * (pre[v] * S[k][v]);
                 pre[v] *= R[v];
             }
-            gnormalise<Q>(x, mask);
+            gnormalise<Q>(x, mask, zsum_of(A, f));
             if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + e) * Q + g * V, x);
             if constexpr (METHOD == kDirect) to_relabelled<Q>(x, A.c.eh[e], sc, mask, g, ex, lg);
             else to_deviation<Q>(x, A.c.eh[e], sc, mask, g, ex, lg);

@@ -31,18 +31,18 @@ __device__ __forceinline__ float gsum_regs(const float (&x)[Q]) {
     for (int g = 0; g < G; g++) {
         float a = 0.f;
 #pragma unroll
-        for (int i = 0; i < V; i++) a += x[g * V + i];
+        for (int i = 0; i < V; i++) a = __fadd_rn(a, x[g * V + i]);
         s[g] = a;
     }
 #pragma unroll
     for (int m = 1; m < G; m <<= 1)
 #pragma unroll
-        for (int g = 0; g < G; g += 2 * m) s[g] = s[g] + s[g + m];
+        for (int g = 0; g < G; g += 2 * m) s[g] = __fadd_rn(s[g], s[g + m]);
     return s[0];
 }
 
 template <int Q>
-__device__ __forceinline__ void gnormalise_regs(float (&x)[Q]) {
+__device__ __forceinline__ void gnormalise_regs(float (&x)[Q], int* zs = nullptr) {
     const float s = gsum_regs<Q>(x);
     if (s > 0.f && s <= 3.0e38f) {
         const float r = 1.0f / s;
@@ -51,6 +51,7 @@ __device__ __forceinline__ void gnormalise_regs(float (&x)[Q]) {
     } else {
 #pragma unroll
         for (int i = 0; i < Q; i++) x[i] = 1.0f / Q;
+        note_zero_sum<1>(zs);
     }
 }
 
@@ -133,7 +134,7 @@ __device__ __forceinline__ void pus_check_regs(const DecodeArgs& A, float* slab,
         float R[Q];
 #pragma unroll
         for (int a = 0; a < Q; a++) R[a] = row[z ^ s_mul[h * Q + a]];   // both below Q
-        gnormalise_regs<Q>(R);
+        gnormalise_regs<Q>(R, zsum_of(A, f));
         stq_g<Q>(slab + (size_t)(e0 + k) * Q, R);
     }
 }
@@ -177,7 +178,7 @@ __device__ __forceinline__ void pus_var_regs(const DecodeArgs& A, float* slab, i
         float Qj[Q];
 #pragma unroll
         for (int i = 0; i < Q; i++) Qj[i] = p[i] * acc[i];
-        gnormalise_regs<Q>(Qj);
+        gnormalise_regs<Q>(Qj, zsum_of(A, f));
         int bi = 0;
         float bv = Qj[0];
 #pragma unroll
@@ -209,7 +210,7 @@ __device__ __forceinline__ void pus_var_regs(const DecodeArgs& A, float* slab, i
             x[i] = p[i] * (pre[i] * S[i]);
             pre[i] *= rk[i];
         }
-        gnormalise_regs<Q>(x);
+        gnormalise_regs<Q>(x, zsum_of(A, f));
         const int e = A.c.cedge[c0 + k];
         if (A.step) stq<Q>(A.msg_io + ((size_t)f * A.c.E + e) * Q, x);
         // stored form: qt[y] = q[h^-1 y]

@@ -91,27 +91,16 @@ __host__ __device__ constexpr size_t res_slab_floats(long long E, int M) {
 }
 
 // r[a] = s[z XOR h a] through the vector's own slot (the calling thread wrote
-// s there), normalised by tree_sum order, written back to the slot.
-template <int Q>
-__device__ __forceinline__ void res_finish_r(float* slot, const float (&s)[Q], int z, int h, const uint8_t* s_mul) {
-    sts_q<Q>(slot, s);
-    float R[Q];
-#pragma unroll
-    for (int a = 0; a < Q; a++) R[a] = slot[z ^ s_mul[h * Q + a]];   // both below Q
-    normalise_regs<Q>(R);
-    sts_q<Q>(slot, R);
-}
-
-// The same with the normalisation in the lane-group order (gsum), as the PUS
-// kernels do.
+// s there), normalised in the lane-group order (gsum) as the PUS kernels do,
+// written back to the slot.
 template <int Q>
 __device__ __forceinline__ void res_finish_r_g(float* slot, const float (&s)[Q], int z, int h,
-                                               const uint8_t* s_mul) {
+                                               const uint8_t* s_mul, int* zs) {
     sts_q<Q>(slot, s);
     float R[Q];
 #pragma unroll
     for (int a = 0; a < Q; a++) R[a] = slot[z ^ s_mul[h * Q + a]];
-    gnormalise_regs<Q>(R);
+    gnormalise_regs<Q>(R, zs);
     sts_q<Q>(slot, R);
 }
 
@@ -306,7 +295,7 @@ struct ResPusCode {
 // while their slots hold the prefixes.
 template <int Q, int DC>
 __device__ __forceinline__ void res_pus_check(const ResPusCode& C, float* X, int i, const uint8_t* s_z,
-                                              const uint8_t* s_mul) {
+                                              const uint8_t* s_mul, int* zs) {
     const int e0 = C.rowptr[i];
     const int d = C.rowptr[i + 1] - e0;
     const int z = s_z ? (s_z[i] & (Q - 1)) : 0;
@@ -316,7 +305,7 @@ __device__ __forceinline__ void res_pus_check(const ResPusCode& C, float* X, int
         float s[Q];
 #pragma unroll
         for (int y = 0; y < Q; y++) s[y] = y == 0 ? 1.f : 0.f;
-        res_finish_r_g<Q>(D, s, z, C.eh[e0], s_mul);
+        res_finish_r_g<Q>(D, s, z, C.eh[e0], s_mul, zs);
         return;
     }
     // forward: prefixes into the inner slots
@@ -337,21 +326,21 @@ __device__ __forceinline__ void res_pus_check(const ResPusCode& C, float* X, int
     // backward: suffixes in registers, r into every slot
     float S[Q];
     lds_q<Q>(S, D + (size_t)(d - 1) * Q);
-    res_finish_r_g<Q>(D + (size_t)(d - 1) * Q, P, z, C.eh[e0 + d - 1], s_mul);
+    res_finish_r_g<Q>(D + (size_t)(d - 1) * Q, P, z, C.eh[e0 + d - 1], s_mul, zs);
 #pragma unroll
     for (int k = DC - 2; k >= 1; k--) {
         if (k < d - 1) {
             float Pk[Q], out[Q];
             lds_q<Q>(Pk, D + (size_t)k * Q);
             xconv_pk<Q>(out, Pk, S);
-            res_finish_r_g<Q>(D + (size_t)k * Q, out, z, C.eh[e0 + k], s_mul);
+            res_finish_r_g<Q>(D + (size_t)k * Q, out, z, C.eh[e0 + k], s_mul, zs);
             float S2[Q];
             xconv_pk<Q>(S2, S, inner[k - 1]);
 #pragma unroll
             for (int y = 0; y < Q; y++) S[y] = S2[y];
         }
     }
-    res_finish_r_g<Q>(D, S, z, C.eh[e0], s_mul);
+    res_finish_r_g<Q>(D, S, z, C.eh[e0], s_mul, zs);
 }
 
 // Vertical pass for column j (Eqs. 4-5) in the arithmetic of pus_var_regs; p
@@ -397,7 +386,7 @@ __device__ __forceinline__ void res_pus_var(const DecodeArgs& A, const ResPusCod
         float Qj[Q];
 #pragma unroll
         for (int i = 0; i < Q; i++) Qj[i] = p[i] * acc[i];
-        gnormalise_regs<Q>(Qj);
+        gnormalise_regs<Q>(Qj, zsum_of(A, f));
         const int bi = argmax_regs<Q>(Qj);
         s_xh[j] = (uint8_t)bi;
 #pragma unroll
@@ -431,7 +420,7 @@ __device__ __forceinline__ void res_pus_var(const DecodeArgs& A, const ResPusCod
                 x[i] = p[i] * (pre[i] * S[i]);
                 pre[i] *= R[i];
             }
-            gnormalise_regs<Q>(x);
+            gnormalise_regs<Q>(x, zsum_of(A, f));
             if (A.step) stq<Q>(A.msg_io + ((size_t)f * A.c.E + A.c.cedge[c0 + k]) * Q, x);
             res_store_relabelled<Q>(X + so[k], x, C.ch[c0 + k], s_div);
         }
@@ -483,7 +472,7 @@ __device__ __forceinline__ void res_pus_frame(const DecodeArgs& A, int f, const 
     __syncthreads();
     int t = 1, ok = 0;
     for (;; t++) {
-        for (int i = tid; i < M; i += T) res_pus_check<Q, DC>(C, X, i, s_z, s_mul);
+        for (int i = tid; i < M; i += T) res_pus_check<Q, DC>(C, X, i, s_z, s_mul, zsum_of(A, f));
         __syncthreads();
         {
             // each column's likelihood is loaded one column ahead
@@ -614,7 +603,7 @@ __device__ __forceinline__ void res_pair_load(ResPair<Q>& w, const DecodeArgs& A
 // (level_check_run's arithmetic with the partials in the slab's slots).
 template <int Q, bool SM>
 __device__ __forceinline__ void res_sus_check(const float* X, const uint8_t* s_z, const ResPair<Q>& w,
-                                              const uint8_t* s_mul, float* row) {
+                                              const uint8_t* s_mul, float* row, int* zs) {
     if (w.rb.z == 0) return;   // a column without checks
     const int4 in = w.ra;
     const int t = in.x - in.y;
@@ -642,7 +631,7 @@ __device__ __forceinline__ void res_sus_check(const float* X, const uint8_t* s_z
     st_lrow<Q>(row, U);
     float R[Q];
     gather_row<Q>(R, row, s_mul + h * Q, z);   // r[a] = s[z XOR h a]
-    normalise_regs<Q>(R);
+    normalise_regs<Q>(R, zs);
     st_lrow<Q>(row, R);
 }
 
@@ -686,7 +675,7 @@ __device__ __forceinline__ void res_sus_var(const DecodeArgs& A, int f, float* X
             if (k2 != k) other[i] *= r[i];
         }
     }
-    normalise_regs<Q>(all);
+    normalise_regs<Q>(all, k == 0 ? zsum_of(A, f) : nullptr);
     const int bi = argmax_regs<Q>(all);
     if (k == 0) {
         s_xh[j] = (uint8_t)bi;
@@ -696,7 +685,7 @@ __device__ __forceinline__ void res_sus_var(const DecodeArgs& A, int f, float* X
     if (d == 0) return;
     const int so = sus_slot<Q, SM>(in.x, in.w);
     s_hx[so / Q] = s_mul[h * Q + bi];
-    normalise_regs<Q>(other);
+    normalise_regs<Q>(other, zsum_of(A, f));
     if (A.step) stq<Q>(A.msg_io + ((size_t)f * A.c.E + in.x) * Q, other);
     // stored form qt[y] = q[h^-1 y]
     st_lrow<Q>(scr, other);
@@ -809,7 +798,7 @@ __device__ __forceinline__ void res_sus_frame(const DecodeArgs& A, int f, const 
             nxt.rb = make_int4(0, 0, 0, 0);
             if (tid < s_lp[pn + 1] - s_lp[pn]) res_pair_load<Q>(nxt, A, f, s_lp[pn] + tid);
             float* row = s_rows + ((cur.rb.y >> 8) & 255) * RS;
-            if (tid < n) res_sus_check<Q, SM>(X, s_z, cur, s_mul, row);
+            if (tid < n) res_sus_check<Q, SM>(X, s_z, cur, s_mul, row, zsum_of(A, f));
             __syncthreads();
             if (tid < n) {
                 float* sc = SM ? X + sus_slot<Q, SM>(cur.ra.x, cur.ra.w) : scr;

@@ -145,6 +145,22 @@ size_t footprint(const Req& r, size_t* ws_out) {
            a256((size_t)r.F * N) + a256((size_t)r.F * 4) + a256((size_t)r.F);
 }
 
+// Iterations a frame of this code may advance in one round: round_iters for
+// frames whose iteration costs at most as much as a GF(16), N = 1000 frame's
+// (the unit below: edge-vector entries times the check node's work per entry,
+// q for the probability route, 4 log2 q for the transforms), proportionally
+// fewer for costlier ones, at least one.  A round lasts as long as its
+// slowest frame, so without the cap one GF(256), N = 8192 request would hold
+// every light request for round_iters of its own iterations.
+int round_iters_for(const CodeDev& c, int method, int round_iters) {
+    int lg = 0;
+    while ((1 << lg) < c.q) lg++;
+    const double work = (double)c.E * c.q * (method == kDirect ? (double)c.q : 4.0 * lg);
+    const double unit = 3000.0 * 16 * 16;
+    const double n = round_iters * unit / (work > 0 ? work : 1.0);
+    return n >= round_iters ? round_iters : (n < 1.0 ? 1 : (int)n);
+}
+
 // Put an admitted request on the device: inputs, state, channel likelihoods
 // and initial messages.  Runs on the worker thread, on the server stream.
 gfbp_status setup(gfbp_server* S, Req& r) {
@@ -174,7 +190,7 @@ gfbp_status setup(gfbp_server* S, Req& r) {
                            S->stream);
     if (e != cudaSuccess) return GFBP_EINVAL;
     r.A.fstate = reinterpret_cast<int*>(base + r.o_state);
-    r.A.round_iters = S->round_iters;
+    r.A.round_iters = round_iters_for(r.code->dev, method, S->round_iters);
     e = launch_channel(r.A, S->stream);
     if (e == cudaSuccess && r.A.markov) e = launch_fill_prior(r.A, S->stream);
     if (e == cudaSuccess && r.schedule == GFBP_SUS) e = launch_init_dev(r.A, S->stream);

@@ -60,8 +60,9 @@ __device__ __forceinline__ void sus_column_tail(const DecodeArgs& A, float* slab
     const int N = A.c.N;
     // E: transform route, the combined deviations; probability route, the
     // distribution of the other edges' sum.  Afterwards E holds r_ij.
-    if constexpr (METHOD == kDirect) direct_finish_n<Q, DV>(E, h, z, d, sc, mask, g, ex, lg);
-    else dev_finish_n<Q, DV>(E, C, h, z, d, sc, mask, g, ex, lg);
+    int* zs = zsum_of(A, f);
+    if constexpr (METHOD == kDirect) direct_finish_n<Q, DV>(E, h, z, d, sc, mask, g, ex, lg, zs);
+    else dev_finish_n<Q, DV>(E, C, h, z, d, sc, mask, g, ex, lg, zs);
     float p[V];
     prior_vec<Q>(A, f, j, p, mask, g);
     float S[DV][V], acc[V];
@@ -81,7 +82,7 @@ __device__ __forceinline__ void sus_column_tail(const DecodeArgs& A, float* slab
         float Qj[V];
 #pragma unroll
         for (int v = 0; v < V; v++) Qj[v] = p[v] * acc[v];
-        gnormalise<Q>(Qj, mask);
+        gnormalise<Q>(Qj, mask, zs);
         const int a = gargmax<Q>(Qj, mask, g);
         if (g == 0) xh[j] = (uint8_t)a;
         if (A.post) stv<V>(A.post + ((size_t)f * N + j) * Q + g * V, Qj);
@@ -107,7 +108,7 @@ __device__ __forceinline__ void sus_column_tail(const DecodeArgs& A, float* slab
 #pragma unroll
     for (int k = 0; k < DV; k++) {
         if (k < d) {
-            gnormalise<Q>(E[k], mask);
+            gnormalise<Q>(E[k], mask, zs);
             if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + eid[k]) * Q + g * V, E[k]);
         }
     }

@@ -217,12 +217,12 @@ __device__ __forceinline__ float tree_sum(const float (&x)[Q]) {
 #pragma unroll
     for (int w = 1; w < Q; w <<= 1)
 #pragma unroll
-        for (int i = 0; i < Q; i += 2 * w) s[i] = s[i] + s[i + w];
+        for (int i = 0; i < Q; i += 2 * w) s[i] = __fadd_rn(s[i], s[i + w]);
     return s[0];
 }
 
 template <int Q>
-__device__ __forceinline__ void normalise_regs(float (&x)[Q]) {
+__device__ __forceinline__ void normalise_regs(float (&x)[Q], int* zs = nullptr) {
     const float s = tree_sum<Q>(x);
     if (s > 0.f && s <= 3.0e38f) {
         const float r = 1.0f / s;
@@ -231,6 +231,7 @@ __device__ __forceinline__ void normalise_regs(float (&x)[Q]) {
     } else {
 #pragma unroll
         for (int i = 0; i < Q; i++) x[i] = 1.0f / Q;
+        note_zero_sum<1>(zs);
     }
 }
 
@@ -275,7 +276,7 @@ __device__ __forceinline__ void level_check(const DecodeArgs& A, int f, const fl
     st_lrow<Q>(row, U);
     float R[Q];
     gather_row<Q>(R, row, s_mul + h * Q, z);   // r[a] = s[z XOR h a]
-    normalise_regs<Q>(R);
+    normalise_regs<Q>(R, zsum_of(A, f));
     st_lrow<Q>(row, R);
 }
 
@@ -314,7 +315,7 @@ __device__ __forceinline__ void level_check_run(const DecodeArgs& A, int f, cons
     st_lrow<Q>(row, U);
     float R[Q];
     gather_row<Q>(R, row, s_mul + h * Q, z);   // r[a] = s[z XOR h a]
-    normalise_regs<Q>(R);
+    normalise_regs<Q>(R, zsum_of(A, f));
     st_lrow<Q>(row, R);
 }
 
@@ -388,7 +389,7 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
         }
     }
     if (k == 0) {
-        normalise_regs<Q>(all);
+        normalise_regs<Q>(all, zsum_of(A, f));
         int bi = 0;
         float bv = all[0];
 #pragma unroll
@@ -399,7 +400,7 @@ __device__ __forceinline__ void level_var(const DecodeArgs& A, int f, float* sla
         if (si >= 0) stq<Q>(A.Qsrc + ((size_t)f * A.K + si) * Q, all);
     }
     if (d == 0) return;
-    normalise_regs<Q>(other);
+    normalise_regs<Q>(other, zsum_of(A, f));
     if (A.step) stq<Q>(A.msg_io + ((size_t)f * A.c.E + in.x) * Q, other);
     // stored form: qt[y] = q[h^-1 y]
     st_lrow<Q>(orow, other);

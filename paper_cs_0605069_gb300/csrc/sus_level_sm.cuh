@@ -142,15 +142,15 @@ __device__ __forceinline__ float sm_sum(const float (&x)[SmLay<Q>::V], unsigned 
 #pragma unroll
     for (int w = 1; w < V; w <<= 1)
 #pragma unroll
-        for (int i = 0; i < V; i += 2 * w) s[i] = s[i] + s[i + w];
+        for (int i = 0; i < V; i += 2 * w) s[i] = __fadd_rn(s[i], s[i + w]);
     float t = s[0];
 #pragma unroll
-    for (int o = 1; o < G; o <<= 1) t = t + __shfl_xor_sync(mask, t, o);
+    for (int o = 1; o < G; o <<= 1) t = __fadd_rn(t, __shfl_xor_sync(mask, t, o));
     return t;
 }
 
 template <int Q>
-__device__ __forceinline__ void sm_normalise(float (&x)[SmLay<Q>::V], unsigned mask) {
+__device__ __forceinline__ void sm_normalise(float (&x)[SmLay<Q>::V], unsigned mask, int* zs = nullptr) {
     constexpr int V = SmLay<Q>::V;
     const float s = sm_sum<Q>(x, mask);
     if (s > 0.f && s <= 3.0e38f) {
@@ -160,6 +160,7 @@ __device__ __forceinline__ void sm_normalise(float (&x)[SmLay<Q>::V], unsigned m
     } else {
 #pragma unroll
         for (int i = 0; i < V; i++) x[i] = 1.0f / Q;
+        note_zero_sum<SmLay<Q>::G>(zs);
     }
 }
 
@@ -204,7 +205,7 @@ __device__ __forceinline__ void sm_suffixes(int M, const int* s_rowptr, float* X
 // Step 1 for the pair of record (ra, rb): r of the column's k-th check into row.
 template <int Q>
 __device__ __forceinline__ void sm_check(const float* X, const uint8_t* s_z, int4 ra, int4 rb, const uint8_t* s_mul,
-                                         float* row, float* scr, unsigned mask, int g) {
+                                         float* row, float* scr, unsigned mask, int g, int* zs) {
     constexpr int V = SmLay<Q>::V;
     if (rb.z == 0) return;   // a column without checks
     const int t = ra.x - ra.y;
@@ -230,7 +231,7 @@ __device__ __forceinline__ void sm_check(const float* X, const uint8_t* s_z, int
     float R[V];
 #pragma unroll
     for (int v = 0; v < V; v++) R[v] = scr[(z ^ s_mul[h * Q + g * V + v]) & (Q - 1)];
-    sm_normalise<Q>(R, mask);
+    sm_normalise<Q>(R, mask, zs);
     sts_v<Q>(row + g * V, R);
 }
 
@@ -268,14 +269,14 @@ __device__ __forceinline__ void sm_var(const DecodeArgs& A, int f, float* X, flo
         }
     }
     if (k == 0) {
-        sm_normalise<Q>(all, mask);
+        sm_normalise<Q>(all, mask, zsum_of(A, f));
         const int a = sm_argmax<Q>(all, mask, g);
         if (g == 0) s_xh[j] = (uint8_t)a;
         if (A.post) sts_v<Q>(A.post + ((size_t)f * N + j) * Q + g * V, all);
         if (si >= 0) sts_v<Q>(A.Qsrc + ((size_t)f * A.K + si) * Q + g * V, all);
     }
     if (d == 0) return;
-    sm_normalise<Q>(other, mask);
+    sm_normalise<Q>(other, mask, zsum_of(A, f));
     if (A.step) sts_v<Q>(A.msg_io + ((size_t)f * A.c.E + ra.x) * Q + g * V, other);
     // stored form: qt[y] = q[h^-1 y]
     sts_v<Q>(scr + g * V, other);
@@ -411,7 +412,7 @@ __device__ __forceinline__ bool sus_level_sm_frame(const DecodeArgs& A, int f, c
                     si = A.src_index[rb.x];
                     if (si >= 0) ldg_vv<Q>(Pm, A.P + ((size_t)f * A.K + si) * Q + g * V);
                 }
-                sm_check<Q>(X, s_z, ra, rb, s_mul, row, scr, mask, g);
+                sm_check<Q>(X, s_z, ra, rb, s_mul, row, scr, mask, g, zsum_of(A, f));
             }
             __syncthreads();
             float pl2[V] = {};

@@ -93,7 +93,8 @@ __device__ __forceinline__ void level_tc_check(const DecodeArgs& A, const float*
 // Step 3: r from the check's inverse transform s (row, scaled by 1/q).
 template <int Q>
 __device__ __forceinline__ void level_tc_finish(const DecodeArgs& A, const uint8_t* zf, int2 pr, float* row,
-                                                unsigned mask, int g, const uint8_t* ex, const uint8_t* lg) {
+                                                unsigned mask, int g, const uint8_t* ex, const uint8_t* lg,
+                                                int* zs) {
     constexpr int V = Lay<Q>::V;
     if (A.c.colptr[pr.x + 1] == A.c.colptr[pr.x]) return;   // a column without checks
     const int4 in = A.c.cinfo[A.c.colptr[pr.x] + pr.y];
@@ -103,7 +104,7 @@ __device__ __forceinline__ void level_tc_finish(const DecodeArgs& A, const uint8
 #pragma unroll
     for (int v = 0; v < V; v++) R[v] = fmaxf(row[(z ^ gf_mul(ex, lg, h, g * V + v)) & (Q - 1)], 0.0f);
     __syncwarp(mask);
-    gnormalise<Q>(R, mask);
+    gnormalise<Q>(R, mask, zs);
     stv<V>(row + g * V, R);
 }
 
@@ -148,7 +149,7 @@ __device__ __forceinline__ void level_tc_var(const DecodeArgs& A, int f, uint8_t
         }
 #pragma unroll
         for (int v = 0; v < V; v++) Qj[v] = p[v] * (S[v] * r[v]);
-        gnormalise<Q>(Qj, mask);
+        gnormalise<Q>(Qj, mask, zsum_of(A, f));
         const int a = gargmax<Q>(Qj, mask, g);
         if (g == 0) xh[j] = (uint8_t)a;
         if (A.post) stv<V>(A.post + ((size_t)f * N + j) * Q + g * V, Qj);
@@ -165,7 +166,7 @@ __device__ __forceinline__ void level_tc_var(const DecodeArgs& A, int f, uint8_t
     float x[V];
 #pragma unroll
     for (int v = 0; v < V; v++) x[v] = p[v] * (pre[v] * S[v]);
-    gnormalise<Q>(x, mask);
+    gnormalise<Q>(x, mask, zsum_of(A, f));
     if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + in.x) * Q + g * V, x);
     // relabelled: qt[b] = q[h^-1 b]
     const int h = (in.z >> 8) & 255;
@@ -221,7 +222,8 @@ __device__ __forceinline__ void sus_level_tc_frame(const DecodeArgs& A, int f, c
                 tc_wht_rows<Q>(hi, lo, rs, n, rows, Q, 1.0f / Q, warp, T / 32);
                 __syncthreads();
                 for (int lp = grp; lp < n; lp += NG)
-                    level_tc_finish<Q>(A, zf, A.c.lpair[s + lp], rows + (size_t)lp * Q, mask, g, s_exp, s_log);
+                    level_tc_finish<Q>(A, zf, A.c.lpair[s + lp], rows + (size_t)lp * Q, mask, g, s_exp, s_log,
+                                       zsum_of(A, f));
                 __syncthreads();
                 for (int lp = grp; lp < n; lp += NG)
                     level_tc_var<Q>(A, f, xh, A.c.lpair[s + lp], rows + (size_t)lp * Q, hi + (size_t)lp * S,

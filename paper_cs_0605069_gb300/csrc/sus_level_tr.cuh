@@ -37,7 +37,7 @@ constexpr int level_tr_sub() {
 template <int Q, int METHOD>
 __device__ __forceinline__ void level_tr_check(const DecodeArgs& A, const float* slab, const uint8_t* zf, int2 pr,
                                                float* row, float* sc, unsigned mask, int g, const uint8_t* ex,
-                                               const uint8_t* lg) {
+                                               const uint8_t* lg, int* zs) {
     constexpr int V = Lay<Q>::V, G = Lay<Q>::G;
     const int j = pr.x, k = pr.y;
     if (A.c.colptr[j + 1] == A.c.colptr[j]) return;   // a column without checks
@@ -69,7 +69,7 @@ __device__ __forceinline__ void level_tr_check(const DecodeArgs& A, const float*
 #pragma unroll
             for (int v = 0; v < V; v++) E[0][v] = (g * V + v) == 0 ? 1.f : 0.f;
         }
-        direct_finish_n<Q, 1>(E, h, z, 1, sc, mask, g, ex, lg);
+        direct_finish_n<Q, 1>(E, h, z, 1, sc, mask, g, ex, lg, zs);
         stv<V>(row + g * V, E[0]);
         return;
     }
@@ -87,7 +87,7 @@ __device__ __forceinline__ void level_tr_check(const DecodeArgs& A, const float*
         dev_combine<V>(E[0], Y);
     }
     C[0] = __shfl_sync(mask, C[0], lane0);
-    dev_finish_n<Q, 1>(E, C, h, z, 1, sc, mask, g, ex, lg);
+    dev_finish_n<Q, 1>(E, C, h, z, 1, sc, mask, g, ex, lg, zs);
     stv<V>(row + g * V, E[0]);
 }
 
@@ -137,7 +137,7 @@ __device__ __forceinline__ void level_tr_var(const DecodeArgs& A, int f, float* 
         float Qj[V];
 #pragma unroll
         for (int v = 0; v < V; v++) Qj[v] = p[v] * acc[v];
-        gnormalise<Q>(Qj, mask);
+        gnormalise<Q>(Qj, mask, zsum_of(A, f));
         const int a = gargmax<Q>(Qj, mask, g);
         if (g == 0) xh[j] = (uint8_t)a;
         if (A.post) stv<V>(A.post + ((size_t)f * N + j) * Q + g * V, Qj);
@@ -150,7 +150,7 @@ __device__ __forceinline__ void level_tr_var(const DecodeArgs& A, int f, float* 
     float x[1][V];
 #pragma unroll
     for (int v = 0; v < V; v++) x[0][v] = p[v] * (pre[v] * S[v]);
-    gnormalise<Q>(x[0], mask);
+    gnormalise<Q>(x[0], mask, zsum_of(A, f));
     if (A.step) stv<V>(A.msg_io + ((size_t)f * A.c.E + in.x) * Q + g * V, x[0]);
     const int h[1] = {(in.z >> 8) & 255};
     if constexpr (METHOD == kDirect) to_relabelled_n<Q, 1>(x, h, 1, sc, mask, g, ex, lg);
@@ -190,7 +190,7 @@ __device__ __forceinline__ void sus_level_tr_frame(const DecodeArgs& A, int f, c
                 const int n = e - s;
                 for (int lp = grp; lp < n; lp += NG)
                     level_tr_check<Q, METHOD>(A, slab, zf, A.c.lpair[s + lp], s_rows + (size_t)lp * Q, sc, mask, g, s_exp,
-                                      s_log);
+                                              s_log, zsum_of(A, f));
                 __syncthreads();
                 for (int lp = grp; lp < n; lp += NG)
                     level_tr_var<Q, METHOD>(A, f, slab, xh, A.c.lpair[s + lp], s_rows + (size_t)lp * Q, sc, mask, g, s_exp,

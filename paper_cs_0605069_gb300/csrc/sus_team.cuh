@@ -72,16 +72,16 @@ __device__ __forceinline__ void xconv_team(float (&out)[V], const float* sa, con
 template <int GS, int V>
 __device__ __forceinline__ float slot_sum(const float (&x)[V], unsigned smask) {
     float s;
-    if constexpr (V == 4) s = (x[0] + x[1]) + (x[2] + x[3]);
-    else if constexpr (V == 2) s = x[0] + x[1];
+    if constexpr (V == 4) s = __fadd_rn(__fadd_rn(x[0], x[1]), __fadd_rn(x[2], x[3]));
+    else if constexpr (V == 2) s = __fadd_rn(x[0], x[1]);
     else s = x[0];
 #pragma unroll
-    for (int m = 1; m < GS; m <<= 1) s += __shfl_xor_sync(smask, s, m);
+    for (int m = 1; m < GS; m <<= 1) s = __fadd_rn(s, __shfl_xor_sync(smask, s, m));
     return s;
 }
 
 template <int Q, int GS, int V>
-__device__ __forceinline__ void slot_normalise(float (&x)[V], unsigned smask) {
+__device__ __forceinline__ void slot_normalise(float (&x)[V], unsigned smask, int* zs = nullptr) {
     const float s = slot_sum<GS, V>(x, smask);
     if (s > 0.f && s <= 3.0e38f) {
         const float r = 1.0f / s;
@@ -90,6 +90,7 @@ __device__ __forceinline__ void slot_normalise(float (&x)[V], unsigned smask) {
     } else {
 #pragma unroll
         for (int v = 0; v < V; v++) x[v] = 1.0f / Q;
+        note_zero_sum<GS>(zs);
     }
 }
 
@@ -214,7 +215,7 @@ __device__ __forceinline__ void team_column(const DecodeArgs& A, int f, int j, c
 #pragma unroll
     for (int v = 0; v < V; v++) R[v] = sa[(z ^ s_mul[h * Q + g * V + v]) & (Q - 1)];
     __syncwarp(smask);
-    slot_normalise<Q, GS, V>(R, smask);
+    slot_normalise<Q, GS, V>(R, smask, act ? zsum_of(A, f) : nullptr);
     if (!act) {
 #pragma unroll
         for (int v = 0; v < V; v++) R[v] = 1.f;
@@ -245,7 +246,7 @@ __device__ __forceinline__ void team_column(const DecodeArgs& A, int f, int j, c
             if (k2 != k) other[v] *= r2;
         }
     }
-    slot_normalise<Q, GS, V>(all, smask);
+    slot_normalise<Q, GS, V>(all, smask, k == 0 ? zsum_of(A, f) : nullptr);
     if (k == 0) {
         const int a = slot_argmax<GS, V>(all, smask, g);
         if (g == 0) xh[j] = (uint8_t)a;
@@ -255,7 +256,7 @@ __device__ __forceinline__ void team_column(const DecodeArgs& A, int f, int j, c
             if (si >= 0) stv<V>(A.Qsrc + ((size_t)f * A.K + si) * Q + g * V, all);
         }
     }
-    slot_normalise<Q, GS, V>(other, smask);
+    slot_normalise<Q, GS, V>(other, smask, act ? zsum_of(A, f) : nullptr);
     if (act && A.step) stv<V>(A.msg_io + ((size_t)f * E + in.x) * Q + g * V, other);
     // stored form: qt[y] = q[h^-1 y]
     stv<V>(sa + g * V, other);

@@ -29,7 +29,7 @@ PARTIALS = {"auto": 0, "fold": 1, "running": 2, "running_global": 3}
 EXPORTS = ("gfbp_last_error", "gfbp_code_create", "gfbp_code_destroy", "gfbp_code_info", "gfbp_level_schedule",
            "gfbp_workspace_size", "gfbp_decode", "gfbp_step", "gfbp_decode_noalloc",
            "gfbp_batch_create", "gfbp_batch_run", "gfbp_batch_variants", "gfbp_batch_set_variants",
-           "gfbp_batch_destroy", "gfbp_autotune", "gfbp_wht",
+           "gfbp_batch_destroy", "gfbp_autotune", "gfbp_wht", "gfbp_wait_selftest",
            "gfbp_server_create", "gfbp_server_submit", "gfbp_server_wait", "gfbp_server_stats",
            "gfbp_server_drain", "gfbp_server_destroy")
 
@@ -52,7 +52,8 @@ class gfbp_options(C.Structure):
     _fields_ = [("punct", C.c_void_p), ("syndrome", C.c_void_p), ("post", C.c_void_p),
                 ("xhat_trace", C.c_void_p), ("no_early_stop", C.c_int32), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("kernel_events", C.c_void_p * 2), ("check_method", C.c_int32),
-                ("sus_width", C.c_int32), ("layout", C.c_int32), ("sus_partials", C.c_int32)]
+                ("sus_width", C.c_int32), ("layout", C.c_int32), ("sus_partials", C.c_int32),
+                ("zero_sums", C.c_void_p)]
 
 
 def lib() -> C.CDLL:
@@ -79,8 +80,9 @@ def lib() -> C.CDLL:
                                     C.POINTER(gfbp_options), P]
             L.gfbp_decode_noalloc.argtypes = L.gfbp_decode.argtypes
             L.gfbp_wht.argtypes = [P, P, i64, i32, i32, P]
+            L.gfbp_wait_selftest.argtypes = [i32, C.POINTER(i32), P]
             for fn in ("gfbp_code_create", "gfbp_code_info", "gfbp_workspace_size", "gfbp_decode", "gfbp_step",
-                       "gfbp_decode_noalloc", "gfbp_wht"):
+                       "gfbp_decode_noalloc", "gfbp_wht", "gfbp_wait_selftest"):
                 getattr(L, fn).restype = C.c_int
             _lib = L
     return _lib
@@ -185,10 +187,11 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
            T=None, K: int = 0, src_pos=None, frame_param=None, punct=None, syndrome=None, post: bool = False,
            trace: bool = False, no_early_stop: bool = False, workspace=None, out=None, stream=None,
            kernel_events=None, check_method: str = "auto", sus_width: int = 0,
-           layout: str = "auto", partials: str = "auto", gauss_seidel: bool = False):
+           layout: str = "auto", partials: str = "auto", gauss_seidel: bool = False, zero_sums: bool = False):
     """gfbp_decode on CUDA tensors.  obs: float32 [F][N][p] (or [F][N][q] for
     loglik).  Returns dict of device tensors x_hat [F][N] uint8, iters [F]
-    int32, converged [F] uint8 (+ post [F][N][q], trace [F][max_iter][N]).
+    int32, converged [F] uint8 (+ post [F][N][q], trace [F][max_iter][N],
+    zero_sums [F] int32: the normalisations that fell back to uniform).
     layout: "auto", "lanes" or "thread" (kernels for q = 4, 8, 16 with the
     direct check node, same results); sus_width: SUS lane teams per frame of
     the "lanes" layout (0 = automatic); partials: "auto", "fold", "running" or
@@ -206,6 +209,8 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
             out["post"] = torch.empty((F, code.N, code.q), dtype=torch.float32, device=dev)
         if trace:
             out["trace"] = torch.empty((F, max_iter, code.N), dtype=torch.uint8, device=dev)
+        if zero_sums:
+            out["zero_sums"] = torch.empty(F, dtype=torch.int32, device=dev)
     pr, _keep = _prior(T, K, src_pos, gauss_seidel)
     if workspace is None:
         nbytes = workspace_size(code, F, schedule, T, K, src_pos)
@@ -216,6 +221,7 @@ def decode(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: 
     opt.sus_width = int(sus_width)
     opt.layout = LAYOUT[layout]
     opt.sus_partials = PARTIALS[partials]
+    opt.zero_sums = _ptr(out.get("zero_sums"))
     if kernel_events is not None:   # (torch.cuda.Event, torch.cuda.Event) timing the schedule kernel alone
         for ev in kernel_events:    # torch creates the CUDA event on its first record
             if not ev.cuda_event:
@@ -268,6 +274,18 @@ def wht(x, method: str = "simt", out=None, stream=None):
     y = torch.empty_like(x) if out is None else out
     _ok(lib().gfbp_wht(_ptr(x), _ptr(y), n, q, WHT_METHOD[method], _stream(stream)), "gfbp_wht")
     return y
+
+
+WAIT = {"mbarrier": 0, "watermark": 1}
+
+
+def wait_selftest(which: str, stream=None):
+    """gfbp_wait_selftest: run one of the kernels' bounded waits on a
+    condition that never comes true.  Returns (status, completed): the
+    expected outcome is (GFBP_ETIMEOUT, 0)."""
+    done = C.c_int32(-1)
+    rc = lib().gfbp_wait_selftest(WAIT[which], C.byref(done), _stream(stream))
+    return int(rc), int(done.value)
 
 
 def decode_noalloc(code: Code, obs, channel: str = "bsc", param: float = 0.0, schedule: str = "pus",

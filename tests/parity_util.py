@@ -134,6 +134,20 @@ def classify_final(gpu, ora, gap_thr=TIE_GAP, horizon=None):
     return np.array(kinds)
 
 
+def fail_report(gpu, ora, hz, frames):
+    """Where each failing frame first left the oracle's decisions on a firm symbol."""
+    out = []
+    for f in frames:
+        t = int(min(gpu["iters"][f], ora["iters"][f]))
+        dis = gpu["trace"][f, :t] != ora["trace_x"][f, :t]
+        firm = dis & (ora["trace_gap"][f, :t] > TIE_GAP)
+        it = np.nonzero(firm.any(1))[0]
+        first = int(it[0]) + 1 if it.size else None
+        out.append(f"frame {f}: iters gpu {gpu['iters'][f]} oracle {ora['iters'][f]}, horizon {hz[f]}, "
+                   f"first firm disagreement at iteration {first}")
+    return "; ".join(out)
+
+
 class Batchlike:
     """The fields of a workload batch that the free-running parity check reads,
     for inputs built in a test (i.i.d. source)."""

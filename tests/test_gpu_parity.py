@@ -17,7 +17,7 @@ parity_util.oracle_horizon); both kinds are counted and reported.
 import numpy as np
 import pytest
 
-from tests.parity_util import LOCKSTEP_ATOL, TIE_GAP, classify_frames, gpu_decode, oracle_horizon, to_dev
+from tests.parity_util import LOCKSTEP_ATOL, TIE_GAP, classify_frames, fail_report, gpu_decode, oracle_horizon, to_dev
 
 # The transform route's stated accuracy (not the default path's bar).
 TRANSFORM_ATOL = {"pus": 1e-4, "sus": 1e-3}
@@ -134,23 +134,9 @@ def _free_running(oracle, b, kind, schedule, method="auto", max_horizon_frac=0.0
     kinds = classify_frames(gpu, ora, horizon=hz)
     n = {k: int((kinds == k).sum()) for k in ("match", "tie", "horizon", "fail")}
     print(f"{schedule}/{method}: frames {len(kinds)} {n}")
-    assert n["fail"] == 0, _fail_report(gpu, ora, hz, np.nonzero(kinds == "fail")[0][:5])
+    assert n["fail"] == 0, fail_report(gpu, ora, hz, np.nonzero(kinds == "fail")[0][:5])
     assert n["horizon"] <= max_horizon_frac * len(kinds) + 1
     return kinds
-
-
-def _fail_report(gpu, ora, hz, frames):
-    """Where each failing frame first left the oracle's decisions on a firm symbol."""
-    out = []
-    for f in frames:
-        t = int(min(gpu["iters"][f], ora["iters"][f]))
-        dis = gpu["trace"][f, :t] != ora["trace_x"][f, :t]
-        firm = dis & (ora["trace_gap"][f, :t] > TIE_GAP)
-        it = np.nonzero(firm.any(1))[0]
-        first = int(it[0]) + 1 if it.size else None
-        out.append(f"frame {f}: iters gpu {gpu['iters'][f]} oracle {ora['iters'][f]}, horizon {hz[f]}, "
-                   f"first firm disagreement at iteration {first}")
-    return "; ".join(out)
 
 
 @pytest.mark.parametrize("schedule", ["pus", "sus"])

@@ -188,6 +188,26 @@ def test_syndrome_form_is_relabelled_codeword_form(oracle, schedule):
         np.testing.assert_allclose(c["post"][f], np.take_along_axis(a["post"][f], idx, 1), atol=1e-12)
 
 
+@pytest.mark.parametrize("schedule", ["pus", "sus"])
+@pytest.mark.parametrize("q", [2, 4])
+def test_zero_sums_count_contradicted_posteriors(oracle, schedule, q):
+    """One check x_0 + x_1 = z over two symbols observed without erasure as
+    (0, 0), with z = 1: in every iteration the check tells each symbol the
+    other value (r = delta at 1), each column's only message q_ij is its own
+    likelihood (it meets no other check), and each posterior Q_j = p_j r_ij
+    vanishes and falls back to uniform: two zero sums per iteration, the
+    decisions (0, 0) (lowest symbol of a uniform posterior), never converged."""
+    code = _code([0, 0], [0, 1], [1, 1], 1, 2, q)
+    obs = np.zeros((1, 2, q.bit_length() - 1), np.float32)   # BEC, every bit seen as 0
+    z = np.array([[1]], np.uint8)
+    for T in (1, 3, 7):
+        a = oracle.decode(code, obs, "bec", 0.0, schedule, max_iter=T, syn=z)
+        assert a["zero_sums"][0] == 2 * T and a["iters"][0] == T and a["conv"][0] == 0
+        np.testing.assert_array_equal(a["xhat"][0], [0, 0])
+    a = oracle.decode(code, obs, "bec", 0.0, schedule, max_iter=5, syn=np.zeros((1, 1), np.uint8))
+    assert a["zero_sums"][0] == 0 and a["iters"][0] == 1 and a["conv"][0] == 1
+
+
 def test_converged_words_satisfy_all_checks(oracle):
     from paper_cs_0605069_gb300 import workload as W
     b = W.make_batch("gf4_n96_bsc005", frames=200)
