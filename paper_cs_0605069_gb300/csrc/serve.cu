@@ -116,6 +116,9 @@ struct gfbp_server {
     cudaStream_t stream = nullptr;
     std::unique_ptr<PoolAlloc> alloc;
     LaunchBufs bufs[2];
+    int* d_states = nullptr;   // one round's frame states, gathered (device)
+    int* h_states = nullptr;   // and read back in one copy (pinned host)
+    int states_cap = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Req*> queue;
@@ -197,8 +200,25 @@ gfbp_status setup(gfbp_server* S, Req& r) {
     return e == cudaSuccess ? GFBP_OK : GFBP_ECUDA;
 }
 
-// Build and launch one schedule's mixed kernel over the resident requests.
-cudaError_t launch_round(gfbp_server* S, int schedule, const std::vector<Req*>& rs) {
+// Frame states of a round's launch in its frame-table order (item it's frames
+// at prefix[it] ..), written at out, so that the host reads every resident
+// frame's state in one copy instead of one per request.
+__global__ void k_gather_states(const DecodeArgs* __restrict__ items, const int* __restrict__ prefix, int n_items,
+                                int total, int* __restrict__ out) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_items - 1;   // the item whose frames hold g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        out[g] = items[lo].fstate[g - prefix[lo]];
+    }
+}
+
+// Build and launch one schedule's mixed kernel over the resident requests;
+// `order` receives them in the launch's item order.
+cudaError_t launch_round(gfbp_server* S, int schedule, const std::vector<Req*>& rs, std::vector<Req*>* order) {
     std::vector<DecodeArgs> items;
     std::vector<int> prefix(1, 0), variant;
     int owner[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
@@ -209,8 +229,10 @@ cudaError_t launch_round(gfbp_server* S, int schedule, const std::vector<Req*>& 
         sel.push_back(r);
         cd.push_back(&r->code->dev);
     }
+    order->clear();
     for (int i : heavy_first(cd)) {
         Req* r = sel[i];
+        order->push_back(r);
         const int pf = r->code->dev.p - 1;
         if (owner[pf] < 0) owner[pf] = (int)items.size();
         items.push_back(r->A);
@@ -296,23 +318,50 @@ void worker_main(gfbp_server* S) {
             S->cv_done.notify_all();
         }
         if (round.empty()) continue;
-        cudaError_t e = launch_round(S, GFBP_SUS, round);
-        if (e == cudaSuccess) e = launch_round(S, GFBP_PUS, round);
-        // frame states of every resident request
-        std::vector<std::vector<int>> st(round.size());
-        for (size_t i = 0; i < round.size() && e == cudaSuccess; i++) {
-            st[i].resize(round[i]->F);
-            e = cudaMemcpyAsync(st[i].data(), round[i]->A.fstate, sizeof(int) * round[i]->F, cudaMemcpyDeviceToHost,
-                                S->stream);
+        std::vector<Req*> order[2];   // SUS, PUS: the resident requests in launch order
+        cudaError_t e = launch_round(S, GFBP_SUS, round, &order[0]);
+        if (e == cudaSuccess) e = launch_round(S, GFBP_PUS, round, &order[1]);
+        // frame states of every resident request: gathered on the device in
+        // launch order, read back in one copy
+        int total = 0;
+        for (int k = 0; k < 2; k++)
+            for (Req* r : order[k]) total += r->F;
+        if (e == cudaSuccess && total > S->states_cap) {
+            if (S->d_states) cudaFree(S->d_states);
+            if (S->h_states) cudaFreeHost(S->h_states);
+            S->d_states = nullptr;
+            S->h_states = nullptr;
+            S->states_cap = 0;
+            const int cap = std::max(total, 2 * S->states_cap + 1024);
+            e = cudaMalloc(&S->d_states, sizeof(int) * (size_t)cap);
+            if (e == cudaSuccess) e = cudaMallocHost(&S->h_states, sizeof(int) * (size_t)cap);
+            if (e == cudaSuccess) S->states_cap = cap;
         }
+        int at = 0;
+        for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+            const MixedLaunch& m = S->bufs[k == 0 ? GFBP_SUS : GFBP_PUS].m;
+            int n = 0;
+            for (Req* r : order[k]) n += r->F;
+            if (n == 0) continue;
+            const int blocks = std::min((n + 255) / 256, 1024);
+            k_gather_states<<<blocks, 256, 0, S->stream>>>(m.d_args, m.d_prefix, m.n_items, n, S->d_states + at);
+            e = cudaGetLastError();
+            at += n;
+        }
+        if (e == cudaSuccess && total > 0)
+            e = cudaMemcpyAsync(S->h_states, S->d_states, sizeof(int) * (size_t)total, cudaMemcpyDeviceToHost,
+                                S->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
         std::vector<Req*> done;
-        for (size_t i = 0; i < round.size(); i++) {
-            Req* r = round[i];
-            r->rounds++;
-            bool all = e == cudaSuccess;
-            for (int f = 0; f < r->F && all; f++) all = (st[i][f] >> 30) != 0;
-            if (all || e != cudaSuccess) done.push_back(r);
+        at = 0;
+        for (int k = 0; k < 2; k++) {
+            for (Req* r : order[k]) {
+                r->rounds++;
+                bool all = e == cudaSuccess;
+                for (int f = 0; f < r->F && all; f++) all = (S->h_states[at + f] >> 30) != 0;
+                at += r->F;
+                if (all || e != cudaSuccess) done.push_back(r);
+            }
         }
         for (Req* r : done) {
             const uint8_t* base = static_cast<const uint8_t*>(S->pool) + r->off;
@@ -484,6 +533,8 @@ extern "C" void gfbp_server_destroy(gfbp_server* S) {
     if (S->worker.joinable()) S->worker.join();
     for (auto& b : S->bufs)
         if (b.dmem) cudaFree(b.dmem);
+    if (S->d_states) cudaFree(S->d_states);
+    if (S->h_states) cudaFreeHost(S->h_states);
     cudaStreamDestroy(S->stream);
     cudaFree(S->pool);
     delete S;
