@@ -487,6 +487,33 @@ def run_paper(args):
     print(json.dumps(line), flush=True)
 
 
+def fig1_trajectory(P0, P, iters):
+    """P[f][t], t = 0..max_iter, for the Fig. 1 statistic: P0 [F] the fraction
+    of symbols the channel alone decides correctly, P [F][max_iter] the
+    fraction after each iteration; after a frame stops (iters [F]) its last
+    iteration's value holds."""
+    P = np.asarray(P, np.float64)
+    F, T = P.shape
+    it = np.asarray(iters, np.int64)
+    last = P[np.arange(F), np.maximum(it - 1, 0)]
+    P = np.where(np.arange(T)[None, :] < it[:, None], P, last[:, None])
+    return np.concatenate([np.asarray(P0, np.float64)[:, None], P], 1)
+
+
+def fig1_gains(Pall, iters, bins):
+    """Sum and count of the gains dP = P_t - P_{t-1} over the iterations each
+    frame ran, binned by the level P_{t-1} they start from (bins: edges)."""
+    dP = np.diff(Pall, axis=1)
+    Pprev = Pall[:, :-1]
+    live = np.arange(dP.shape[1])[None, :] < np.asarray(iters)[:, None]
+    nb = len(bins) - 1
+    b = np.clip(np.digitize(Pprev, bins) - 1, 0, nb - 1)
+    sums, cnts = np.zeros(nb), np.zeros(nb)
+    np.add.at(sums, b[live], dP[live])
+    np.add.at(cnts, b[live], 1)
+    return sums, cnts
+
+
 def run_fig1(args):
     """The statistic of Fig. 1: P = fraction of correctly decided symbols after
     an iteration, dP = its gain in that iteration; the mean gain of PUS over
@@ -523,21 +550,13 @@ def run_fig1(args):
             tr = out["trace"]                                           # [n][max_iter][N], 255 after the stop
             it = out["iters"].long()
             iters[sched].append(it.cpu().numpy())
-            P = (tr == xd[:, None, :]).float().mean(2)                  # [n][max_iter]
-            # after the stop the decision is frozen at the last iteration's
-            last = torch.gather(P, 1, (it - 1).clamp(min=0)[:, None])
-            t_idx = torch.arange(max_iter, device=P.device)[None, :]
-            P = torch.where(t_idx < it[:, None], P, last)
+            P = (tr == xd[:, None, :]).float().mean(2).cpu().numpy()    # [n][max_iter]
             # P before the first iteration: the channel's own decisions
-            P0 = ((torch.from_numpy(np.asarray(obs.cpu().numpy() > 0.5, np.int64)) *
-                   (1 << torch.arange(p))).sum(2).cuda() == xd).float().mean(1)
-            Pall = torch.cat([P0[:, None], P], 1).cpu().numpy()
-            dP = np.diff(Pall, axis=1)
-            Pprev = Pall[:, :-1]
-            live = t_idx.cpu().numpy() < it.cpu().numpy()[:, None]     # iterations that ran
-            b = np.clip(np.digitize(Pprev, bins) - 1, 0, 19)
-            np.add.at(sums[sched], b[live], dP[live])
-            np.add.at(cnts[sched], b[live], 1)
+            x0 = (np.asarray(obs.cpu().numpy() > 0.5, np.int64) * (1 << np.arange(p))).sum(2)
+            P0 = (x0 == x).mean(1)
+            sm, cn = fig1_gains(fig1_trajectory(P0, P, it.cpu().numpy()), it.cpu().numpy(), bins)
+            sums[sched] += sm
+            cnts[sched] += cn
     rows = []
     for k in range(20):
         if cnts["pus"][k] > 0 and cnts["sus"][k] > 0:

@@ -72,3 +72,22 @@ def test_error_rates_by_noise_level(bench):
     assert r["1.0"] == {"fer": 0.5, "ser": 0.5, "ber": 4 / 16, "frames": 2}
     assert r["1.5"] == {"fer": 0.5, "ser": 1 / 8, "ber": 2 / 16, "frames": 2}
     assert r["2.0"]["fer"] == 0.0 and r["all"]["frames"] == 6
+
+
+def test_fig1_statistic_on_a_hand_worked_example():
+    """Fig. 1's statistic: P before the first iteration and after each one,
+    frozen after a frame stops; gains dP over the iterations that ran,
+    binned by the level they start from."""
+    import numpy as np
+    from bench_modes import fig1_gains, fig1_trajectory
+    P0 = np.array([0.5, 0.25])
+    P = np.array([[0.75, 1.0, 0.1],      # frame 0 stopped after 2 iterations (0.1: after the stop)
+                  [0.25, 0.5, 0.75]])
+    iters = np.array([2, 3])
+    Pall = fig1_trajectory(P0, P, iters)
+    np.testing.assert_array_equal(Pall, [[0.5, 0.75, 1.0, 1.0], [0.25, 0.25, 0.5, 0.75]])
+    sums, cnts = fig1_gains(Pall, iters, np.array([0.0, 0.5, 1.0]))
+    # bin [0, 0.5): frame 1's gains from 0.25 (0 and 0.25); bin [0.5, 1]:
+    # frame 0's from 0.5 and 0.75, frame 1's from 0.5 (0.25 each)
+    np.testing.assert_allclose(sums, [0.25, 0.75])
+    np.testing.assert_array_equal(cnts, [2, 3])
