@@ -327,12 +327,12 @@ void worker_main(gfbp_server* S) {
         for (int k = 0; k < 2; k++)
             for (Req* r : order[k]) total += r->F;
         if (e == cudaSuccess && total > S->states_cap) {
+            const int cap = std::max(total, 2 * S->states_cap + 1024);
             if (S->d_states) cudaFree(S->d_states);
             if (S->h_states) cudaFreeHost(S->h_states);
             S->d_states = nullptr;
             S->h_states = nullptr;
             S->states_cap = 0;
-            const int cap = std::max(total, 2 * S->states_cap + 1024);
             e = cudaMalloc(&S->d_states, sizeof(int) * (size_t)cap);
             if (e == cudaSuccess) e = cudaMallocHost(&S->h_states, sizeof(int) * (size_t)cap);
             if (e == cudaSuccess) S->states_cap = cap;
