@@ -497,10 +497,12 @@ typedef struct {
     size_t bytes_in_use, peak_bytes;
 } gfbp_server_stats_t;
 
-/* round_iters >= 1: iterations a resident frame advances per round at most;
- * frames whose iteration costs more than a GF(16), N = 1000 frame's advance
- * proportionally fewer (at least one), so that a round is not held by the
- * costliest request for round_iters of its iterations. */
+/* round_iters >= 1: iterations a resident frame advances per round at most.
+ * Requests whose iteration costs at least eight GF(16), N = 1000 frame
+ * iterations run in a lane of rounds of their own, on their own stream, that
+ * light requests never wait for; in the light lane a frame costing more than
+ * one such unit advances proportionally fewer iterations per round (at
+ * least one). */
 gfbp_status gfbp_server_create(size_t hbm_budget_bytes, int32_t round_iters, gfbp_server** out);
 /* Queue a request (thread-safe).  GFBP_EINVAL if its footprint exceeds the
  * whole budget; GFBP_EBUSY while the server drains.  The output buffers must

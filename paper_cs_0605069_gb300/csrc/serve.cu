@@ -12,6 +12,15 @@
 // are copied to the caller's host buffers, their pool space is freed and
 // their waiters are woken.  Requests that arrive while others run are
 // admitted at the next round boundary and share its launches.
+//
+// Two lanes, each with its own stream, launch tables and state buffers: light
+// requests run in rounds the worker waits for; heavy requests (an iteration
+// costing at least kHeavyUnits GF(16), N = 1000 frame-iterations) run in
+// rounds on their own stream that the worker only polls between light rounds.
+// A round lasts as long as its slowest frame, so without the split every light
+// request would wait for round_iters iterations of the heaviest resident
+// frame.  Requests are set up on a third stream (their pageable copies may
+// wait for it), and a lane's stream waits for the setups before each round.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -98,6 +107,7 @@ struct Req {
     int state = 0;  // 0 queued, 1 resident, 2 done, 3 failed
     gfbp_status status = GFBP_OK;
     int rounds = 0;
+    int lane = 0;   // 0 light, 1 heavy
     Clock::time_point t_submit, t_admit, t_done;
 };
 
@@ -107,22 +117,36 @@ struct LaunchBufs {  // device tables of one round's mixed launch
     MixedLaunch m;
 };
 
+// One lane of rounds (see above).  `resident` is guarded by the server mutex;
+// the rest belongs to the worker thread.
+struct Lane {
+    cudaStream_t stream = nullptr;
+    LaunchBufs bufs[2];
+    int* d_states = nullptr;   // the round's frame states, gathered (device)
+    int* h_states = nullptr;   // and read back in one copy (pinned host)
+    int states_cap = 0;
+    std::vector<Req*> resident;
+    std::vector<Req*> order[2];   // the round in flight: SUS, PUS requests in launch order
+    cudaEvent_t done = nullptr;   // recorded after the round's state copy
+    bool in_flight = false;
+};
+
+constexpr double kHeavyUnits = 8.0;
+
 }  // namespace
 
 struct gfbp_server {
     size_t budget = 0;
     int round_iters = 8;
     void* pool = nullptr;
-    cudaStream_t stream = nullptr;
+    cudaStream_t setup_stream = nullptr;
+    cudaEvent_t setup_done = nullptr;   // recorded after each batch of setups
     std::unique_ptr<PoolAlloc> alloc;
-    LaunchBufs bufs[2];
-    int* d_states = nullptr;   // one round's frame states, gathered (device)
-    int* h_states = nullptr;   // and read back in one copy (pinned host)
-    int states_cap = 0;
+    Lane lane[2];
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Req*> queue;
-    std::vector<Req*> resident;
+    bool admit_blocked = false;   // the queue's head did not fit; cleared when space is freed
     std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
     uint64_t next_id = 1;
     bool stop = false, draining = false;
@@ -148,25 +172,33 @@ size_t footprint(const Req& r, size_t* ws_out) {
            a256((size_t)r.F * N) + a256((size_t)r.F * 4) + a256((size_t)r.F);
 }
 
-// Iterations a frame of this code may advance in one round: round_iters for
-// frames whose iteration costs at most as much as a GF(16), N = 1000 frame's
-// (the unit below: edge-vector entries times the check node's work per entry,
-// q for the probability route, 4 log2 q for the transforms), proportionally
-// fewer for costlier ones, at least one.  A round lasts as long as its
-// slowest frame, so without the cap one GF(256), N = 8192 request would hold
-// every light request for round_iters of its own iterations.
-int round_iters_for(const CodeDev& c, int method, int round_iters) {
+// The check-node route the server runs a code on (AUTO's choice).
+int served_method(const CodeDev& c) { return c.q <= kAutoDirectMaxQ ? kDirect : kTransform; }
+
+// Work of one iteration of one frame of this code in units of a GF(16),
+// N = 1000 frame's iteration: edge-vector entries times the check node's work
+// per entry (q for the probability route, 4 log2 q for the transforms).
+double iteration_units(const CodeDev& c) {
     int lg = 0;
     while ((1 << lg) < c.q) lg++;
-    const double work = (double)c.E * c.q * (method == kDirect ? (double)c.q : 4.0 * lg);
-    const double unit = 3000.0 * 16 * 16;
-    const double n = round_iters * unit / (work > 0 ? work : 1.0);
+    const double work = (double)c.E * c.q * (served_method(c) == kDirect ? (double)c.q : 4.0 * lg);
+    return work / (3000.0 * 16 * 16);
+}
+
+// Iterations a frame advances in one round.  Heavy lane: round_iters.  Light
+// lane: round_iters for frames costing at most one unit, proportionally fewer
+// for costlier ones (at least one), so that a light round lasts about
+// round_iters unit iterations.
+int round_iters_for(const Req& r, int round_iters) {
+    if (r.lane == 1) return round_iters;
+    const double n = round_iters / std::max(iteration_units(r.code->dev), 1e-9);
     return n >= round_iters ? round_iters : (n < 1.0 ? 1 : (int)n);
 }
 
 // Put an admitted request on the device: inputs, state, channel likelihoods
-// and initial messages.  Runs on the worker thread, on the server stream.
+// and initial messages.  Runs on the worker thread, on the setup stream.
 gfbp_status setup(gfbp_server* S, Req& r) {
+    cudaStream_t st = S->setup_stream;
     uint8_t* base = static_cast<uint8_t*>(S->pool) + r.off;
     const size_t N = (size_t)r.code->dev.N;
     size_t o = 0;
@@ -177,26 +209,26 @@ gfbp_status setup(gfbp_server* S, Req& r) {
     r.o_x = o; o += a256((size_t)r.F * N);
     r.o_it = o; o += a256((size_t)r.F * 4);
     r.o_cv = o;
-    cudaError_t e = cudaMemcpyAsync(base + r.o_obs, r.obs.data(), r.obs.size() * 4, cudaMemcpyHostToDevice, S->stream);
+    cudaError_t e = cudaMemcpyAsync(base + r.o_obs, r.obs.data(), r.obs.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !r.fparam.empty())
-        e = cudaMemcpyAsync(base + r.o_fp, r.fparam.data(), r.fparam.size() * 4, cudaMemcpyHostToDevice, S->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + r.o_state, 0, (size_t)r.F * 4, S->stream);
+        e = cudaMemcpyAsync(base + r.o_fp, r.fparam.data(), r.fparam.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + r.o_state, 0, (size_t)r.F * 4, st);
     if (e != cudaSuccess) return GFBP_ECUDA;
     gfbp_channel ch = r.ch;
     ch.frame_param = r.fparam.empty() ? nullptr : reinterpret_cast<const float*>(base + r.o_fp);
     gfbp_prior pr{};
     if (r.markov) { pr.kind = GFBP_PRIOR_MARKOV; pr.T = r.T.data(); pr.K = r.K; pr.src_pos = r.src_pos.data(); }
-    const int method = r.code->dev.q <= kAutoDirectMaxQ ? kDirect : kTransform;
+    const int method = served_method(r.code->dev);
     e = batch_prepare_item(r.A, base + r.o_ws, r.code, r.F, reinterpret_cast<const float*>(base + r.o_obs), ch,
                            (gfbp_schedule)r.schedule, r.markov ? &pr : nullptr, r.max_iter, base + r.o_x,
                            reinterpret_cast<int32_t*>(base + r.o_it), base + r.o_cv, nullptr, method, nullptr,
-                           S->stream);
+                           st);
     if (e != cudaSuccess) return GFBP_EINVAL;
     r.A.fstate = reinterpret_cast<int*>(base + r.o_state);
-    r.A.round_iters = round_iters_for(r.code->dev, method, S->round_iters);
-    e = launch_channel(r.A, S->stream);
-    if (e == cudaSuccess && r.A.markov) e = launch_fill_prior(r.A, S->stream);
-    if (e == cudaSuccess && r.schedule == GFBP_SUS) e = launch_init_dev(r.A, S->stream);
+    r.A.round_iters = round_iters_for(r, S->round_iters);
+    e = launch_channel(r.A, st);
+    if (e == cudaSuccess && r.A.markov) e = launch_fill_prior(r.A, st);
+    if (e == cudaSuccess && r.schedule == GFBP_SUS) e = launch_init_dev(r.A, st);
     return e == cudaSuccess ? GFBP_OK : GFBP_ECUDA;
 }
 
@@ -216,9 +248,9 @@ __global__ void k_gather_states(const DecodeArgs* __restrict__ items, const int*
     }
 }
 
-// Build and launch one schedule's mixed kernel over the resident requests;
-// `order` receives them in the launch's item order.
-cudaError_t launch_round(gfbp_server* S, int schedule, const std::vector<Req*>& rs, std::vector<Req*>* order) {
+// Build and launch one schedule's mixed kernel over a lane's requests on its
+// stream; `order` receives them in the launch's item order.
+cudaError_t launch_round(Lane& L, int schedule, const std::vector<Req*>& rs, std::vector<Req*>* order) {
     std::vector<DecodeArgs> items;
     std::vector<int> prefix(1, 0), variant;
     int owner[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
@@ -240,19 +272,18 @@ cudaError_t launch_round(gfbp_server* S, int schedule, const std::vector<Req*>& 
         variant.push_back(tuned_variant(r->code, schedule));
     }
     if (items.empty()) return cudaSuccess;
-    LaunchBufs& B = S->bufs[schedule];
+    LaunchBufs& B = L.bufs[schedule];
     const int n = (int)items.size();
-    const size_t a_args = a256(sizeof(DecodeArgs) * (size_t)n), a_int = a256(sizeof(int) * (size_t)(n + 1));
     if (n > B.cap) {
         if (B.dmem) cudaFree(B.dmem);
-        B.cap = std::max(n, 2 * B.cap);
-        const size_t cargs = a256(sizeof(DecodeArgs) * (size_t)B.cap), cint = a256(sizeof(int) * (size_t)(B.cap + 1));
+        B.dmem = nullptr;
+        const int cap = std::max(n, 2 * B.cap);
+        const size_t cargs = a256(sizeof(DecodeArgs) * (size_t)cap), cint = a256(sizeof(int) * (size_t)(cap + 1));
         cudaError_t e = cudaMalloc(&B.dmem, cargs + 2 * cint + 512);
         if (e != cudaSuccess) { B.cap = 0; B.dmem = nullptr; return e; }
+        B.cap = cap;
     }
     const size_t cargs = a256(sizeof(DecodeArgs) * (size_t)B.cap), cint = a256(sizeof(int) * (size_t)(B.cap + 1));
-    (void)a_args;
-    (void)a_int;
     uint8_t* base = static_cast<uint8_t*>(B.dmem);
     MixedLaunch& m = B.m;
     m.d_args = reinterpret_cast<DecodeArgs*>(base);
@@ -263,30 +294,123 @@ cudaError_t launch_round(gfbp_server* S, int schedule, const std::vector<Req*>& 
     m.n_items = n;
     m.total = prefix.back();
     m.schedule = schedule;
-    cudaError_t e = cudaMemcpyAsync(m.d_args, items.data(), sizeof(DecodeArgs) * n, cudaMemcpyHostToDevice, S->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_prefix, prefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, S->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_variant, variant.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_field, owner, sizeof(owner), cudaMemcpyHostToDevice, S->stream);
+    cudaError_t e = cudaMemcpyAsync(m.d_args, items.data(), sizeof(DecodeArgs) * n, cudaMemcpyHostToDevice, L.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_prefix, prefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, L.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_variant, variant.data(), sizeof(int) * n, cudaMemcpyHostToDevice, L.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_field, owner, sizeof(owner), cudaMemcpyHostToDevice, L.stream);
     if (e != cudaSuccess) return e;
     mixed_shape(m, variant.data());
-    return mixed_launch(m, S->stream);
+    return mixed_launch(m, L.stream);
+}
+
+// Start a round of a lane over `round` (its resident requests): the launches of
+// both schedules after the setups recorded so far, the frame states gathered in
+// launch order and copied back in one copy, then the lane's event.
+cudaError_t start_round(gfbp_server* S, Lane& L, const std::vector<Req*>& round) {
+    cudaError_t e = cudaStreamWaitEvent(L.stream, S->setup_done, 0);
+    if (e == cudaSuccess) e = launch_round(L, GFBP_SUS, round, &L.order[0]);
+    if (e == cudaSuccess) e = launch_round(L, GFBP_PUS, round, &L.order[1]);
+    int total = 0;
+    for (int k = 0; k < 2; k++)
+        for (Req* r : L.order[k]) total += r->F;
+    if (e == cudaSuccess && total > L.states_cap) {
+        const int cap = std::max(total, 2 * L.states_cap + 1024);
+        if (L.d_states) cudaFree(L.d_states);
+        if (L.h_states) cudaFreeHost(L.h_states);
+        L.d_states = nullptr;
+        L.h_states = nullptr;
+        L.states_cap = 0;
+        e = cudaMalloc(&L.d_states, sizeof(int) * (size_t)cap);
+        if (e == cudaSuccess) e = cudaMallocHost(&L.h_states, sizeof(int) * (size_t)cap);
+        if (e == cudaSuccess) L.states_cap = cap;
+    }
+    int at = 0;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        const MixedLaunch& m = L.bufs[k == 0 ? GFBP_SUS : GFBP_PUS].m;
+        int n = 0;
+        for (Req* r : L.order[k]) n += r->F;
+        if (n == 0) continue;
+        const int blocks = std::min((n + 255) / 256, 1024);
+        k_gather_states<<<blocks, 256, 0, L.stream>>>(m.d_args, m.d_prefix, m.n_items, n, L.d_states + at);
+        e = cudaGetLastError();
+        at += n;
+    }
+    if (e == cudaSuccess && total > 0)
+        e = cudaMemcpyAsync(L.h_states, L.d_states, sizeof(int) * (size_t)total, cudaMemcpyDeviceToHost, L.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(L.done, L.stream);
+    L.in_flight = e == cudaSuccess;
+    return e;
+}
+
+// After a lane's round completed (e: its status): retire the requests whose
+// frames have all stopped — outputs copied to their host buffers, pool space
+// freed (the lane's stream has finished with it), waiters woken.
+void finish_round(gfbp_server* S, Lane& L, cudaError_t e) {
+    L.in_flight = false;
+    std::vector<Req*> done;
+    int at = 0;
+    for (int k = 0; k < 2; k++) {
+        for (Req* r : L.order[k]) {
+            r->rounds++;
+            bool all = e == cudaSuccess;
+            for (int f = 0; f < r->F && all; f++) all = (L.h_states[at + f] >> 30) != 0;
+            at += r->F;
+            if (all || e != cudaSuccess) done.push_back(r);
+        }
+        L.order[k].clear();
+    }
+    for (Req* r : done) {
+        const uint8_t* base = static_cast<const uint8_t*>(S->pool) + r->off;
+        const size_t N = (size_t)r->code->dev.N;
+        if (e == cudaSuccess) {
+            cudaMemcpyAsync(r->hx, base + r->o_x, (size_t)r->F * N, cudaMemcpyDeviceToHost, L.stream);
+            cudaMemcpyAsync(r->hit, base + r->o_it, (size_t)r->F * 4, cudaMemcpyDeviceToHost, L.stream);
+            cudaMemcpyAsync(r->hconv, base + r->o_cv, (size_t)r->F, cudaMemcpyDeviceToHost, L.stream);
+        }
+    }
+    if (!done.empty()) cudaStreamSynchronize(L.stream);
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->rounds++;
+    for (Req* r : done) {
+        r->state = e == cudaSuccess ? 2 : 3;
+        r->status = e == cudaSuccess ? GFBP_OK : GFBP_ECUDA;
+        r->t_done = Clock::now();
+        S->alloc->release(r->off, r->bytes);
+        L.resident.erase(std::find(L.resident.begin(), L.resident.end(), r));
+        S->completed++;
+    }
+    if (!done.empty()) {
+        S->admit_blocked = false;
+        S->cv_done.notify_all();
+    }
+}
+
+bool lanes_idle(const gfbp_server* S) {
+    return S->lane[0].resident.empty() && S->lane[1].resident.empty() && !S->lane[1].in_flight;
 }
 
 void worker_main(gfbp_server* S) {
     cudaSetDevice(S->device);
+    Lane& light = S->lane[0];
+    Lane& heavy = S->lane[1];
     for (;;) {
         std::vector<Req*> admitted;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait_for(lk, std::chrono::milliseconds(20), [&] {
-                return S->stop || !S->queue.empty() || !S->resident.empty();
+            // with a heavy round in flight, poll it every millisecond
+            S->cv_work.wait_for(lk, std::chrono::milliseconds(heavy.in_flight ? 1 : 20), [&] {
+                return S->stop || (!S->queue.empty() && !S->admit_blocked) || !light.resident.empty() ||
+                       (!heavy.resident.empty() && !heavy.in_flight);
             });
-            if (S->stop && S->queue.empty() && S->resident.empty()) break;
+            if (S->stop && S->queue.empty() && lanes_idle(S)) break;
             // admission in arrival order while the footprint fits
             while (!S->queue.empty()) {
                 Req* r = S->queue.front();
                 size_t off = 0;
-                if (!S->alloc->alloc(r->bytes, &off)) break;
+                if (!S->alloc->alloc(r->bytes, &off)) {
+                    S->admit_blocked = true;
+                    break;
+                }
                 S->queue.pop_front();
                 r->off = off;
                 r->t_admit = Clock::now();
@@ -298,92 +422,53 @@ void worker_main(gfbp_server* S) {
             r->status = setup(S, *r);
             if (r->status != GFBP_OK) failed.push_back(r);
         }
-        std::vector<Req*> round;
+        if (!admitted.empty()) cudaEventRecord(S->setup_done, S->setup_stream);
         {
             std::lock_guard<std::mutex> lk(S->mu);
             for (Req* r : admitted)
                 if (r->status == GFBP_OK) {
                     r->state = 1;
-                    S->resident.push_back(r);
+                    S->lane[r->lane].resident.push_back(r);
                 }
-            round = S->resident;
-            S->peak_resident = std::max(S->peak_resident, (int)S->resident.size());
+            S->peak_resident = std::max(S->peak_resident, (int)(light.resident.size() + heavy.resident.size()));
             S->peak_bytes = std::max(S->peak_bytes, S->alloc->used());
         }
+        if (!failed.empty()) cudaStreamSynchronize(S->setup_stream);   // nothing of theirs in flight
         for (Req* r : failed) {
             std::lock_guard<std::mutex> lk(S->mu);
             S->alloc->release(r->off, r->bytes);
+            S->admit_blocked = false;
             r->state = 3;
             r->t_done = Clock::now();
             S->cv_done.notify_all();
         }
-        if (round.empty()) continue;
-        std::vector<Req*> order[2];   // SUS, PUS: the resident requests in launch order
-        cudaError_t e = launch_round(S, GFBP_SUS, round, &order[0]);
-        if (e == cudaSuccess) e = launch_round(S, GFBP_PUS, round, &order[1]);
-        // frame states of every resident request: gathered on the device in
-        // launch order, read back in one copy
-        int total = 0;
-        for (int k = 0; k < 2; k++)
-            for (Req* r : order[k]) total += r->F;
-        if (e == cudaSuccess && total > S->states_cap) {
-            const int cap = std::max(total, 2 * S->states_cap + 1024);
-            if (S->d_states) cudaFree(S->d_states);
-            if (S->h_states) cudaFreeHost(S->h_states);
-            S->d_states = nullptr;
-            S->h_states = nullptr;
-            S->states_cap = 0;
-            e = cudaMalloc(&S->d_states, sizeof(int) * (size_t)cap);
-            if (e == cudaSuccess) e = cudaMallocHost(&S->h_states, sizeof(int) * (size_t)cap);
-            if (e == cudaSuccess) S->states_cap = cap;
+        // heavy lane: collect a finished round, start the next
+        if (heavy.in_flight) {
+            const cudaError_t q = cudaEventQuery(heavy.done);
+            if (q != cudaErrorNotReady) finish_round(S, heavy, q);
         }
-        int at = 0;
-        for (int k = 0; k < 2 && e == cudaSuccess; k++) {
-            const MixedLaunch& m = S->bufs[k == 0 ? GFBP_SUS : GFBP_PUS].m;
-            int n = 0;
-            for (Req* r : order[k]) n += r->F;
-            if (n == 0) continue;
-            const int blocks = std::min((n + 255) / 256, 1024);
-            k_gather_states<<<blocks, 256, 0, S->stream>>>(m.d_args, m.d_prefix, m.n_items, n, S->d_states + at);
-            e = cudaGetLastError();
-            at += n;
-        }
-        if (e == cudaSuccess && total > 0)
-            e = cudaMemcpyAsync(S->h_states, S->d_states, sizeof(int) * (size_t)total, cudaMemcpyDeviceToHost,
-                                S->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-        std::vector<Req*> done;
-        at = 0;
-        for (int k = 0; k < 2; k++) {
-            for (Req* r : order[k]) {
-                r->rounds++;
-                bool all = e == cudaSuccess;
-                for (int f = 0; f < r->F && all; f++) all = (S->h_states[at + f] >> 30) != 0;
-                at += r->F;
-                if (all || e != cudaSuccess) done.push_back(r);
+        if (!heavy.in_flight) {
+            std::vector<Req*> round;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                round = heavy.resident;
+            }
+            if (!round.empty()) {
+                const cudaError_t e = start_round(S, heavy, round);
+                if (e != cudaSuccess) finish_round(S, heavy, e);
             }
         }
-        for (Req* r : done) {
-            const uint8_t* base = static_cast<const uint8_t*>(S->pool) + r->off;
-            const size_t N = (size_t)r->code->dev.N;
-            if (e == cudaSuccess) {
-                cudaMemcpyAsync(r->hx, base + r->o_x, (size_t)r->F * N, cudaMemcpyDeviceToHost, S->stream);
-                cudaMemcpyAsync(r->hit, base + r->o_it, (size_t)r->F * 4, cudaMemcpyDeviceToHost, S->stream);
-                cudaMemcpyAsync(r->hconv, base + r->o_cv, (size_t)r->F, cudaMemcpyDeviceToHost, S->stream);
-            }
+        // light lane: one round, waited for
+        std::vector<Req*> round;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            round = light.resident;
         }
-        if (!done.empty()) cudaStreamSynchronize(S->stream);
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->rounds++;
-        for (Req* r : done) {
-            r->state = e == cudaSuccess ? 2 : 3;
-            r->status = e == cudaSuccess ? GFBP_OK : GFBP_ECUDA;
-            r->t_done = Clock::now();
-            S->alloc->release(r->off, r->bytes);
-            S->resident.erase(std::find(S->resident.begin(), S->resident.end(), r));
-            S->completed++;
+        if (!round.empty()) {
+            cudaError_t e = start_round(S, light, round);
+            if (e == cudaSuccess) e = cudaEventSynchronize(light.done);
+            finish_round(S, light, e);
         }
-        if (!done.empty()) S->cv_done.notify_all();
     }
 }
 
@@ -401,9 +486,20 @@ extern "C" gfbp_status gfbp_server_create(size_t hbm_budget_bytes, int32_t round
     S->round_iters = round_iters;
     cudaGetDevice(&S->device);
     cudaError_t e = cudaMalloc(&S->pool, hbm_budget_bytes);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->setup_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->setup_done, cudaEventDisableTiming);
+    for (Lane& L : S->lane) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         set_error(std::string("gfbp_server_create: ") + cudaGetErrorString(e));
+        for (Lane& L : S->lane) {
+            if (L.done) cudaEventDestroy(L.done);
+            if (L.stream) cudaStreamDestroy(L.stream);
+        }
+        if (S->setup_done) cudaEventDestroy(S->setup_done);
+        if (S->setup_stream) cudaStreamDestroy(S->setup_stream);
         if (S->pool) cudaFree(S->pool);
         delete S;
         return e == cudaErrorMemoryAllocation ? GFBP_ENOMEM : GFBP_ECUDA;
@@ -450,6 +546,7 @@ extern "C" gfbp_status gfbp_server_submit(gfbp_server* S, const gfbp_request* q,
     r->hx = q->x_hat;
     r->hit = q->iters;
     r->hconv = q->converged;
+    r->lane = iteration_units(c->dev) >= kHeavyUnits ? 1 : 0;
     r->bytes = footprint(*r, &r->ws_bytes);
     if (r->bytes > S->budget) {
         set_error("gfbp_server_submit: the request's device footprint (" + std::to_string(r->bytes) +
@@ -504,7 +601,7 @@ extern "C" gfbp_status gfbp_server_stats(gfbp_server* S, gfbp_server_stats_t* ou
     if (!S || !out) { set_error("gfbp_server_stats: NULL argument"); return GFBP_EINVAL; }
     std::lock_guard<std::mutex> lk(S->mu);
     out->queued = (int32_t)S->queue.size();
-    out->resident = (int32_t)S->resident.size();
+    out->resident = (int32_t)(S->lane[0].resident.size() + S->lane[1].resident.size());
     out->peak_resident = S->peak_resident;
     out->rounds = S->rounds;
     out->completed = S->completed;
@@ -518,7 +615,8 @@ extern "C" gfbp_status gfbp_server_drain(gfbp_server* S) {
     std::unique_lock<std::mutex> lk(S->mu);
     S->draining = true;
     S->cv_work.notify_one();
-    while (!S->queue.empty() || !S->resident.empty()) S->cv_done.wait_for(lk, std::chrono::milliseconds(20));
+    while (!S->queue.empty() || !S->lane[0].resident.empty() || !S->lane[1].resident.empty())
+        S->cv_done.wait_for(lk, std::chrono::milliseconds(20));
     return GFBP_OK;
 }
 
@@ -531,11 +629,16 @@ extern "C" void gfbp_server_destroy(gfbp_server* S) {
     }
     S->cv_work.notify_one();
     if (S->worker.joinable()) S->worker.join();
-    for (auto& b : S->bufs)
-        if (b.dmem) cudaFree(b.dmem);
-    if (S->d_states) cudaFree(S->d_states);
-    if (S->h_states) cudaFreeHost(S->h_states);
-    cudaStreamDestroy(S->stream);
+    for (Lane& L : S->lane) {
+        for (auto& b : L.bufs)
+            if (b.dmem) cudaFree(b.dmem);
+        if (L.d_states) cudaFree(L.d_states);
+        if (L.h_states) cudaFreeHost(L.h_states);
+        cudaEventDestroy(L.done);
+        cudaStreamDestroy(L.stream);
+    }
+    cudaEventDestroy(S->setup_done);
+    cudaStreamDestroy(S->setup_stream);
     cudaFree(S->pool);
     delete S;
 }

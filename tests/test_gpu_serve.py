@@ -88,6 +88,47 @@ def test_each_request_decodes_as_alone_while_others_run(env):
         assert res["latency_us"] > 0 and res["rounds"] >= 1
 
 
+def test_heavy_and_light_lanes_decode_as_alone(env):
+    """Requests whose iteration costs eight GF(16), N = 1000 frame-iterations
+    or more (here GF(256), N = 384 and GF(64), N = 1000) run in their own lane
+    of rounds, beside the light ones: every result is still what the request
+    decodes to alone, for requests in both lanes arriving while others run."""
+    torch, gfbp, W = env
+    rng = np.random.default_rng(11)
+    heavy = [W.regular_code(256, 384, cfg="serve_heavy_256", encodable=False),
+             W.regular_code(64, 1000, cfg="serve_heavy_64", encodable=False)]
+    light = [W.regular_code(4, 96, cfg="serve_light_4", encodable=False),
+             W.regular_code(16, 96, cfg="serve_light_16", encodable=False)]
+    reqs = []
+    for k in range(12):
+        code = heavy[(k // 3) % 2] if k % 3 == 0 else light[k % 2]
+        F = 1 + k % 2
+        x = np.zeros((F, code.N), np.int64)
+        sig = W.ebn0_to_sigma(2.0)
+        reqs.append(dict(code=code, obs=W.biawgn(rng, x, code.p, sig), channel="awgn", param=sig, T=None, K=0,
+                         schedule="sus" if k % 2 == 0 else "pus", max_iter=[30, 60][k % 2]))
+    dev_codes = {}
+    for r in reqs:
+        if id(r["code"]) not in dev_codes:
+            dev_codes[id(r["code"])] = gfbp.Code.from_coo(r["code"])
+    srv = gfbp.Server(1 << 30, round_iters=4)
+    ids = [srv.submit(dev_codes[id(r["code"])], r["obs"], r["channel"], r["param"], schedule=r["schedule"],
+                      max_iter=r["max_iter"]) for r in reqs[:6]]
+    first = srv.wait(ids[1])                  # a light request, while the heavy ones run
+    ids += [srv.submit(dev_codes[id(r["code"])], r["obs"], r["channel"], r["param"], schedule=r["schedule"],
+                       max_iter=r["max_iter"]) for r in reqs[6:]]
+    results = {i: srv.wait(i) for i in ids if i != ids[1]}
+    results[ids[1]] = first
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs)
+    for r, i in zip(reqs, ids):
+        ref = _alone(torch, gfbp, dev_codes, r)
+        for k in ("x_hat", "iters", "converged"):
+            np.testing.assert_array_equal(results[i][k], ref[k], err_msg=f"q={r['code'].q} N={r['code'].N} "
+                                                                          f"{r['schedule']} {k}")
+
+
 def test_served_requests_against_the_oracle(env, oracle):
     """Each served request (mixed q, channels, priors, schedules, admitted while
     others are resident) against the FP64 oracle's decode of it (Sec. 2):
