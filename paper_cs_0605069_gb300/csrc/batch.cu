@@ -268,8 +268,11 @@ __global__ void __launch_bounds__(kMixedThreads) k_sus_mixed(const DecodeArgs* _
 // probability-route level kernels of q >= 32 reach on their own (80
 // registers): those items hold most of a mixed batch's work, and two CTAs per
 // SM (128 registers) left a third of their slots empty.
+// With 512 threads (`MixedLaunch::wide`) one CTA per SM: twice the lane groups
+// for each of fewer frames at once, for frames whose levels hold hundreds of
+// pairs.
 template <int NTH>
-__global__ void __launch_bounds__(NTH, NTH == 256 ? 3 : 4) k_sus_mixed_cta(const DecodeArgs* __restrict__ items,
+__global__ void __launch_bounds__(NTH, NTH == 512 ? 1 : (NTH == 256 ? 3 : 4)) k_sus_mixed_cta(const DecodeArgs* __restrict__ items,
                                                                     const int* __restrict__ prefix,
                                                                     const int* __restrict__ variant, int n_items,
                                                                     int total, int* counter, const int* field_item) {
@@ -294,6 +297,20 @@ __global__ void __launch_bounds__(NTH, NTH == 256 ? 3 : 4) k_sus_mixed_cta(const
         const uint8_t* lg = T.lg[pf];
         const uint8_t* mul = T.mul[pf <= 3 ? pf : 0];
         const uint8_t* div = T.div[pf <= 3 ? pf : 0];
+        if constexpr (NTH == 512) {   // the wide form runs the FP32 lane-group variants only
+            switch (var) {
+            case kLevel32T: sus_level_tr_call<32, NTH, kTransform>(A, f, ex, lg, s_dyn); break;
+            case kLevel64T: sus_level_tr_call<64, NTH, kTransform>(A, f, ex, lg, s_dyn); break;
+            case kLevel128T: sus_level_tr_call<128, NTH, kTransform>(A, f, ex, lg, s_dyn); break;
+            case kLevel256T: sus_level_tr_call<256, NTH, kTransform>(A, f, ex, lg, s_dyn); break;
+            case kLevel32D: sus_level_tr_call<32, NTH, kDirect>(A, f, ex, lg, s_dyn); break;
+            case kLevel64D: sus_level_tr_call<64, NTH, kDirect>(A, f, ex, lg, s_dyn); break;
+            case kLevel128D: sus_level_tr_call<128, NTH, kDirect>(A, f, ex, lg, s_dyn); break;
+            case kLevel256D: sus_level_tr_call<256, NTH, kDirect>(A, f, ex, lg, s_dyn); break;
+            default: break;
+            }
+            continue;
+        }
         switch (var) {
         case kLevel2D: sus_level_call<2, NTH>(A, f, mul, div, s_dyn); break;
         case kLevel4D: sus_level_call<4, NTH>(A, f, mul, div, s_dyn); break;
@@ -471,16 +488,24 @@ void mixed_shape(MixedLaunch& m, const int* variants) {
             (cta_variant(variants[i]) ? m.has_cta : m.has_warp) = true;
             if (lane_group_variant(variants[i])) m.cta_threads = 256;
         }
+        // the wide form when every CTA-family item is an FP32 lane-group variant
+        bool wide = m.wide && m.cta_threads == 256;
+        for (int i = 0; i < m.n_items && wide; i++)
+            if (cta_variant(variants[i])) wide = lane_group_variant(variants[i]) && variant_method(variants[i]) != kTensor;
+        if (wide) m.cta_threads = 512;
         m.cta_smem = 0;
         for (int i = 0; i < m.n_items; i++)
-            m.cta_smem = max2(m.cta_smem, m.cta_threads == 256 ? cta_variant_smem<256>(variants[i])
-                                                               : cta_variant_smem<128>(variants[i]));
+            m.cta_smem = max2(m.cta_smem, m.cta_threads == 512   ? cta_variant_smem<512>(variants[i])
+                                          : m.cta_threads == 256 ? cta_variant_smem<256>(variants[i])
+                                                                 : cta_variant_smem<128>(variants[i]));
         kernel_prepare((const void*)k_sus_mixed, kMixedThreads, 0, &occ);
         const long long want = ((long long)m.total + 3) / 4;
         const long long cap = (long long)num_sms() * (occ > 0 ? occ : 1);
         m.grid = (int)(want < cap ? want : cap);
         int occ2 = 1;
-        if (m.cta_threads == 256)
+        if (m.cta_threads == 512)
+            kernel_prepare((const void*)k_sus_mixed_cta<512>, 512, m.cta_smem, &occ2);
+        else if (m.cta_threads == 256)
             kernel_prepare((const void*)k_sus_mixed_cta<256>, 256, m.cta_smem, &occ2);
         else
             kernel_prepare((const void*)k_sus_mixed_cta<128>, 128, m.cta_smem, &occ2);
@@ -501,7 +526,10 @@ cudaError_t mixed_launch(const MixedLaunch& m, cudaStream_t s) {
     if (m.schedule == GFBP_SUS) {
         if (m.has_cta)
         {
-            if (m.cta_threads == 256)
+            if (m.cta_threads == 512)
+                k_sus_mixed_cta<512><<<m.grid_cta, 512, m.cta_smem, s>>>(m.d_args, m.d_prefix, m.d_variant, m.n_items,
+                                                                        m.total, m.d_counter + 1, m.d_field);
+            else if (m.cta_threads == 256)
                 k_sus_mixed_cta<256><<<m.grid_cta, 256, m.cta_smem, s>>>(m.d_args, m.d_prefix, m.d_variant, m.n_items,
                                                                         m.total, m.d_counter + 1, m.d_field);
             else

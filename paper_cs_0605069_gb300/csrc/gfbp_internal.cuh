@@ -684,6 +684,7 @@ struct MixedLaunch {
     int grid_cta = 0;        // SUS: CTA-family kernel (level schedules)
     size_t cta_smem = 0;     // its dynamic shared memory (largest over the items' variants)
     int cta_threads = 128;   // its threads per CTA
+    bool wide = false;       // 512 threads per CTA where 256 would do (frames large enough to use them)
     bool has_cta = false, has_warp = false;
 };
 

@@ -129,6 +129,7 @@ struct Lane {
     std::vector<Req*> order[2];   // the round in flight: SUS, PUS requests in launch order
     cudaEvent_t done = nullptr;   // recorded after the round's state copy
     bool in_flight = false;
+    bool wide = false;   // 512-thread CTAs for the lane-group level kernels (heavy lane)
 };
 
 constexpr double kHeavyUnits = 8.0;
@@ -294,6 +295,7 @@ cudaError_t launch_round(Lane& L, int schedule, const std::vector<Req*>& rs, std
     m.n_items = n;
     m.total = prefix.back();
     m.schedule = schedule;
+    m.wide = L.wide;
     cudaError_t e = cudaMemcpyAsync(m.d_args, items.data(), sizeof(DecodeArgs) * n, cudaMemcpyHostToDevice, L.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_prefix, prefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, L.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m.d_variant, variant.data(), sizeof(int) * n, cudaMemcpyHostToDevice, L.stream);
@@ -484,6 +486,7 @@ extern "C" gfbp_status gfbp_server_create(size_t hbm_budget_bytes, int32_t round
     if (!S) { set_error("gfbp_server_create: out of host memory"); return GFBP_ENOMEM; }
     S->budget = hbm_budget_bytes;
     S->round_iters = round_iters;
+    S->lane[1].wide = true;
     cudaGetDevice(&S->device);
     cudaError_t e = cudaMalloc(&S->pool, hbm_budget_bytes);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->setup_stream, cudaStreamNonBlocking);
