@@ -8,9 +8,8 @@ namespace {
 
 constexpr int kLevelTrThreads = 256;
 
-template <int Q, int METHOD>
-cudaError_t launch_level_tr_qm(const DecodeArgs& A, int num_sms, cudaStream_t s) {
-    constexpr int T = kLevelTrThreads;
+template <int Q, int T, int METHOD>
+cudaError_t launch_level_tr_qmt(const DecodeArgs& A, int num_sms, cudaStream_t s) {
     constexpr size_t smem = level_tr_smem<Q, T>();
     int occ = 0;
     cudaError_t e = kernel_prepare((const void*)k_sus_level_tr<Q, T, METHOD>, T, smem, &occ);
@@ -21,6 +20,18 @@ cudaError_t launch_level_tr_qm(const DecodeArgs& A, int num_sms, cudaStream_t s)
     if (grid < 1) return cudaSuccess;
     k_sus_level_tr<Q, T, METHOD><<<(int)grid, T, smem, s>>>(A);
     return cudaGetLastError();
+}
+
+// 256 threads per frame; with no more frames than SMs (each frame has an SM to
+// itself) 512 for q >= 32, twice the lane groups on every level's pairs: the
+// same results (each pair's arithmetic does not depend on which group runs
+// it), sooner.
+template <int Q, int METHOD>
+cudaError_t launch_level_tr_qm(const DecodeArgs& A, int num_sms, cudaStream_t s) {
+    if constexpr (Q >= 32) {
+        if (A.F <= num_sms) return launch_level_tr_qmt<Q, 512, METHOD>(A, num_sms, s);
+    }
+    return launch_level_tr_qmt<Q, kLevelTrThreads, METHOD>(A, num_sms, s);
 }
 
 // The probability route by lane groups is instantiated for q >= 32 (below, the
